@@ -1,0 +1,415 @@
+/*
+ * Reference oracle for the bmDCA hot path (adabmDCA 2.0, arXiv 2501.18456).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously correct
+ * FP64 restatement of the paper's equations.  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  The CUDA
+ * library shares no code, header, table or helper with it.
+ *
+ * Conventions (readings of the paper where it is silent are listed in the
+ * design notes; each is repeated next to the function it affects):
+ *   - a sequence / chain state is s[0..L-1], s_i in {0..q-1}, gap = 0
+ *     (Sec. 2.3, Table 1: the gap is the first symbol of every alphabet);
+ *   - couplings use the natural layout J[i][j][a][b] = J_ij(a,b), FP64,
+ *     symmetric J_ij(a,b) = J_ji(b,a), J_ii = 0 (Sec. 2.1, after Eq. 1);
+ *   - fields h[i][a] = h_i(a);
+ *   - energy E(s) = -sum_i h_i(s_i) - sum_{i<j} J_ij(s_i,s_j), so that
+ *     p(s) ~ exp(-E(s)) (Eq. 1); each unordered pair counted once;
+ *   - chains are unweighted model samples (Sec. 2.1, "Monte Carlo
+ *     estimation of the gradient").
+ *
+ * Every function is pinned by the CPU tests against something other than
+ * itself (exact enumeration, closed forms, numpy brute force, numpy's
+ * independent Philox implementation).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------
+ * Philox4x64-10 counter-based generator, from its published definition
+ * (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2,
+ * 3", SC'11).  Ten rounds; each round multiplies counter words 0 and 2 by
+ * the two Philox multipliers, takes the high/low halves of the 128-bit
+ * products and mixes them with the other counter words and the round key.
+ * The key is bumped by the two Weyl constants between rounds.
+ * The paper itself only says chains are updated with Gibbs steps; the
+ * generator is this library's choice so that both sides can draw the same
+ * uniforms (keyed by seed, chain, sweep and site).
+ * ---------------------------------------------------------------------- */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(M0, c[0], &hi0, &lo0);
+        mulhilo64(M1, c[2], &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c[1] ^ k0;
+        uint64_t n1 = lo1;
+        uint64_t n2 = hi0 ^ c[3] ^ k1;
+        uint64_t n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* The 24-bit uniform used by every draw: key = (seed, 0), counter =
+ * (chain, sweep, site, tag); the top 24 bits of output word 0.
+ * tag 0 = Gibbs draw, tag 1 = chain initialisation. */
+uint32_t orc_u24(uint64_t seed, uint64_t chain, uint64_t sweep, uint64_t site, uint64_t tag)
+{
+    uint64_t ctr[4] = {chain, sweep, site, tag};
+    uint64_t key[2] = {seed, 0};
+    uint64_t out[4];
+    orc_philox4x64_10(ctr, key, out);
+    return (uint32_t)(out[0] >> 40);
+}
+
+/* ------------------------------------------------------------------------
+ * Chain initialisation: uniformly random sequences (Sec. 2.1, chains
+ * "chosen uniformly at random").  Symbol = floor(u24 * q / 2^24), exact in
+ * integer arithmetic.  chain0 offsets the chain index so that a subset of
+ * chains can be generated.
+ * ---------------------------------------------------------------------- */
+void orc_chains_init(int M, int L, int q, uint64_t seed, uint64_t chain0, uint8_t *s)
+{
+    for (int m = 0; m < M; ++m)
+        for (int i = 0; i < L; ++i) {
+            uint64_t r = orc_u24(seed, chain0 + (uint64_t)m, 0, (uint64_t)i, 1);
+            s[(size_t)m * L + i] = (uint8_t)((r * (uint64_t)q) >> 24);
+        }
+}
+
+static inline size_t jidx(int L, int q, int i, int j, int a, int b)
+{
+    return (((size_t)i * L + j) * q + a) * q + b;
+}
+
+/* ------------------------------------------------------------------------
+ * DCA energy, Eq. 1: E(s) = -sum_i h_i(s_i) - sum_{i<j} J_ij(s_i, s_j).
+ * ---------------------------------------------------------------------- */
+double orc_energy(const double *h, const double *J, int L, int q, const uint8_t *s)
+{
+    double e = 0.0;
+    for (int i = 0; i < L; ++i) e -= h[(size_t)i * q + s[i]];
+    for (int i = 0; i < L; ++i)
+        for (int j = i + 1; j < L; ++j) e -= J[jidx(L, q, i, j, s[i], s[j])];
+    return e;
+}
+
+void orc_energy_batch(const double *h, const double *J, int L, int q, const uint8_t *S, int n, double *E)
+{
+    for (int k = 0; k < n; ++k) E[k] = orc_energy(h, J, L, q, S + (size_t)k * L);
+}
+
+/* Local field of site i given the rest of the sequence (the conditional of
+ * Eq. 1 with every other site fixed):
+ * H_i(a) = h_i(a) + sum_{j != i} J_ij(a, s_j), summed over j ascending. */
+void orc_fields(const double *h, const double *J, int L, int q, const uint8_t *s, int i, double *H)
+{
+    for (int a = 0; a < q; ++a) {
+        double acc = h[(size_t)i * q + a];
+        for (int j = 0; j < L; ++j) {
+            if (j == i) continue;
+            acc += J[jidx(L, q, i, j, a, s[j])];
+        }
+        H[a] = acc;
+    }
+}
+
+/* Categorical draw by inverse CDF from p(a) ~ exp(beta * H(a)) with the
+ * uniform u in [0,1).  Reading (the paper gives no draw rule): subtract the
+ * maximum for range safety, prefix-sum the weights for a ascending, pick
+ * the first a with u * S_total < S_a (q-1 if none).  *margin receives the
+ * distance of u to the nearest interior CDF boundary S_a / S_total. */
+int orc_draw(const double *H, int q, double beta, double u, double *margin)
+{
+    double w[64], S[64];
+    double mx = -INFINITY;
+    for (int a = 0; a < q; ++a) if (beta * H[a] > mx) mx = beta * H[a];
+    double acc = 0.0;
+    for (int a = 0; a < q; ++a) {
+        w[a] = exp(beta * H[a] - mx);
+        acc += w[a];
+        S[a] = acc;
+    }
+    double t = u * S[q - 1];
+    int pick = q - 1;
+    for (int a = 0; a < q; ++a)
+        if (t < S[a]) { pick = a; break; }
+    if (margin) {
+        double mg = INFINITY;
+        for (int a = 0; a < q - 1; ++a) {
+            double d = fabs(u - S[a] / S[q - 1]);
+            if (d < mg) mg = d;
+        }
+        *margin = mg;
+    }
+    return pick;
+}
+
+/* Conditional distribution P(s_i = a | s_{-i}) at inverse temperature beta. */
+void orc_conditional(const double *h, const double *J, int L, int q, const uint8_t *s, int i,
+                     double beta, double *P)
+{
+    double H[64];
+    orc_fields(h, J, L, q, s, i, H);
+    double mx = -INFINITY, Z = 0.0;
+    for (int a = 0; a < q; ++a) if (beta * H[a] > mx) mx = beta * H[a];
+    for (int a = 0; a < q; ++a) { P[a] = exp(beta * H[a] - mx); Z += P[a]; }
+    for (int a = 0; a < q; ++a) P[a] /= Z;
+}
+
+/* ------------------------------------------------------------------------
+ * Persistent-chain Gibbs sampling (Sec. 2.1, "Monte Carlo estimation of
+ * the gradient"; a sweep proposes every site once, Sec. 3.4 "Number of
+ * Monte Carlo steps").  Reading: sites visited in order 0..L-1 every sweep;
+ * sweep counter = sweep0 + k, never repeated over a run.
+ * ---------------------------------------------------------------------- */
+void orc_gibbs(const double *h, const double *J, int L, int q, int M, uint8_t *S,
+               uint64_t seed, uint64_t chain0, uint64_t sweep0, int nsweeps, double beta)
+{
+    double H[64];
+    for (int k = 0; k < nsweeps; ++k)
+        for (int m = 0; m < M; ++m) {
+            uint8_t *s = S + (size_t)m * L;
+            for (int i = 0; i < L; ++i) {
+                orc_fields(h, J, L, q, s, i, H);
+                uint32_t r = orc_u24(seed, chain0 + (uint64_t)m, sweep0 + (uint64_t)k, (uint64_t)i, 0);
+                double u = (double)r * (1.0 / 16777216.0);
+                s[i] = (uint8_t)orc_draw(H, q, beta, u, NULL);
+            }
+        }
+}
+
+/* Teacher-forced check of one sweep produced elsewhere.  For every chain
+ * and site i (in order) the oracle conditions on after[j] for j < i and on
+ * before[j] for j > i -- exactly what a correct sequential sweep conditions
+ * on -- draws with the same uniform and compares with after[i].
+ * Returns the number of site-updates that disagree; *max_margin receives
+ * the largest oracle margin among the disagreements (0 if none) and
+ * *min_margin the smallest margin over all site-updates. */
+long orc_gibbs_verify(const double *h, const double *J, int L, int q, int M,
+                      const uint8_t *before, const uint8_t *after, uint64_t seed,
+                      uint64_t chain0, uint64_t sweep, double beta,
+                      double *max_margin, double *min_margin)
+{
+    double H[64];
+    uint8_t *s = (uint8_t *)malloc((size_t)L);
+    long bad = 0;
+    double mxm = 0.0, mnm = INFINITY;
+    for (int m = 0; m < M; ++m) {
+        memcpy(s, before + (size_t)m * L, (size_t)L);
+        for (int i = 0; i < L; ++i) {
+            orc_fields(h, J, L, q, s, i, H);
+            uint32_t r = orc_u24(seed, chain0 + (uint64_t)m, sweep, (uint64_t)i, 0);
+            double u = (double)r * (1.0 / 16777216.0);
+            double mg;
+            int pick = orc_draw(H, q, beta, u, &mg);
+            if (mg < mnm) mnm = mg;
+            uint8_t got = after[(size_t)m * L + i];
+            if (got != pick) {
+                ++bad;
+                if (mg > mxm) mxm = mg;
+            }
+            s[i] = got;
+        }
+    }
+    free(s);
+    if (max_margin) *max_margin = mxm;
+    if (min_margin) *min_margin = mnm;
+    return bad;
+}
+
+/* ------------------------------------------------------------------------
+ * Model statistics from the chains, unweighted (Sec. 2.1: p_i, p_ij are
+ * estimated by the chain frequencies).  Integer counts over the upper
+ * block triangle i <= j, block (i,j) at index i*L - i*(i-1)/2 + (j-i),
+ * each block q x q row-major [a][b] = #{m : s_i = a, s_j = b}.
+ * ---------------------------------------------------------------------- */
+void orc_chain_stats(const uint8_t *S, int M, int L, int q, int32_t *C)
+{
+    size_t nblk = (size_t)L * (L + 1) / 2;
+    memset(C, 0, nblk * q * q * sizeof(int32_t));
+    for (int m = 0; m < M; ++m) {
+        const uint8_t *s = S + (size_t)m * L;
+        for (int i = 0; i < L; ++i)
+            for (int j = i; j < L; ++j) {
+                size_t p = (size_t)i * L - (size_t)i * (i - 1) / 2 + (size_t)(j - i);
+                C[p * q * q + (size_t)s[i] * q + s[j]] += 1;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Importance weights, Eq. 3 (Sec. 2.3): w_m = 1 / N_m with N_m the number
+ * of sequences n (m itself included) whose identity with m -- the count of
+ * positions with equal symbols, gaps included -- is at least thr.
+ * The caller passes the integer threshold thr = ceil(seqid * L).
+ * M_eff = sum_m w_m (Sec. 3.4, "Regularization").
+ * ---------------------------------------------------------------------- */
+void orc_seq_weights(const uint8_t *X, int N, int L, int thr, double *w, double *meff)
+{
+    double tot = 0.0;
+    for (int m = 0; m < N; ++m) {
+        long cnt = 0;
+        for (int n = 0; n < N; ++n) {
+            int id = 0;
+            for (int i = 0; i < L; ++i) id += (X[(size_t)m * L + i] == X[(size_t)n * L + i]);
+            if (id >= thr) ++cnt;
+        }
+        w[m] = 1.0 / (double)cnt;
+    }
+    for (int m = 0; m < N; ++m) tot += w[m];
+    *meff = tot;
+}
+
+/* ------------------------------------------------------------------------
+ * Weighted data frequencies, Eq. 2, followed by the pseudocount of
+ * Eqs. 4-5: f_i = (1-alpha) f_i^data + alpha/q,
+ *            f_ij = (1-alpha) f_ij^data + alpha/q^2  (i != j).
+ * w == NULL means uniform weights (M_eff = N).  Full layout
+ * fij[i][j][a][b]; reading for the unused diagonal blocks:
+ * fij[i][i][a][b] = delta_ab f_i(a).
+ * ---------------------------------------------------------------------- */
+void orc_data_stats(const uint8_t *X, const double *w, int N, int L, int q, double alpha,
+                    double *fi, double *fij)
+{
+    double meff = 0.0;
+    for (int m = 0; m < N; ++m) meff += w ? w[m] : 1.0;
+    memset(fi, 0, (size_t)L * q * sizeof(double));
+    memset(fij, 0, (size_t)L * L * q * q * sizeof(double));
+    for (int m = 0; m < N; ++m) {
+        double wm = w ? w[m] : 1.0;
+        const uint8_t *s = X + (size_t)m * L;
+        for (int i = 0; i < L; ++i) {
+            fi[(size_t)i * q + s[i]] += wm;
+            for (int j = 0; j < L; ++j)
+                if (j != i) fij[jidx(L, q, i, j, s[i], s[j])] += wm;
+        }
+    }
+    for (size_t k = 0; k < (size_t)L * q; ++k) fi[k] = (1.0 - alpha) * (fi[k] / meff) + alpha / q;
+    for (int i = 0; i < L; ++i)
+        for (int j = 0; j < L; ++j)
+            for (int a = 0; a < q; ++a)
+                for (int b = 0; b < q; ++b) {
+                    size_t k = jidx(L, q, i, j, a, b);
+                    if (i == j)
+                        fij[k] = (a == b) ? fi[(size_t)i * q + a] : 0.0;
+                    else
+                        fij[k] = (1.0 - alpha) * (fij[k] / meff) + alpha / ((double)q * q);
+                }
+}
+
+/* ------------------------------------------------------------------------
+ * Convergence check (Sec. 2.1, "Convergence criterium"): Pearson
+ * correlation between C^data_ij(a,b) = f_ij(a,b) - f_i(a) f_j(b) and
+ * C^model_ij(a,b) = p_ij(a,b) - p_i(a) p_j(b), over i < j and all (a,b).
+ * p from the chain counts C (layout of orc_chain_stats) divided by M.
+ * Plain two-pass formula (means first, then centred sums).
+ * ---------------------------------------------------------------------- */
+static double *orc_single_from_counts(const int32_t *C, int M, int L, int q)
+{
+    double *pi = (double *)malloc((size_t)L * q * sizeof(double));
+    for (int i = 0; i < L; ++i) {
+        size_t p = (size_t)i * L - (size_t)i * (i - 1) / 2;   /* diagonal block (i,i) */
+        for (int a = 0; a < q; ++a) {
+            long c = 0;
+            for (int b = 0; b < q; ++b) c += C[p * q * q + (size_t)a * q + b];
+            pi[(size_t)i * q + a] = (double)c / M;
+        }
+    }
+    return pi;
+}
+
+double orc_pearson(const double *fi, const double *fij, const int32_t *C, int M, int L, int q)
+{
+    double *pi = orc_single_from_counts(C, M, L, q);
+    double n = 0.0, sx = 0.0, sy = 0.0;
+    /* pass 1: means */
+    for (int i = 0; i < L; ++i)
+        for (int j = i + 1; j < L; ++j) {
+            size_t p = (size_t)i * L - (size_t)i * (i - 1) / 2 + (size_t)(j - i);
+            for (int a = 0; a < q; ++a)
+                for (int b = 0; b < q; ++b) {
+                    double x = fij[jidx(L, q, i, j, a, b)] - fi[(size_t)i * q + a] * fi[(size_t)j * q + b];
+                    double y = (double)C[p * q * q + (size_t)a * q + b] / M
+                               - pi[(size_t)i * q + a] * pi[(size_t)j * q + b];
+                    sx += x; sy += y; n += 1.0;
+                }
+        }
+    double mx = sx / n, my = sy / n;
+    double sxx = 0.0, syy = 0.0, sxy = 0.0;
+    /* pass 2: centred second moments */
+    for (int i = 0; i < L; ++i)
+        for (int j = i + 1; j < L; ++j) {
+            size_t p = (size_t)i * L - (size_t)i * (i - 1) / 2 + (size_t)(j - i);
+            for (int a = 0; a < q; ++a)
+                for (int b = 0; b < q; ++b) {
+                    double x = fij[jidx(L, q, i, j, a, b)] - fi[(size_t)i * q + a] * fi[(size_t)j * q + b];
+                    double y = (double)C[p * q * q + (size_t)a * q + b] / M
+                               - pi[(size_t)i * q + a] * pi[(size_t)j * q + b];
+                    sxx += (x - mx) * (x - mx);
+                    syy += (y - my) * (y - my);
+                    sxy += (x - mx) * (y - my);
+                }
+        }
+    free(pi);
+    return sxy / sqrt(sxx * syy);
+}
+
+/* ------------------------------------------------------------------------
+ * Boltzmann-learning step, Eq. 9 ("params update"):
+ *   h_i(a)    += lr (f_i(a)    - p_i(a))
+ *   J_ij(a,b) += lr (f_ij(a,b) - p_ij(a,b))   for i != j; J_ii stays 0.
+ * p from the counts (layout of orc_chain_stats) divided by M; the (j,i)
+ * entry is the same pair statistic transposed, keeping J symmetric.
+ * ---------------------------------------------------------------------- */
+void orc_update(double *h, double *J, const double *fi, const double *fij, const int32_t *C,
+                int M, double lr, int L, int q)
+{
+    double *pi = orc_single_from_counts(C, M, L, q);
+    for (size_t k = 0; k < (size_t)L * q; ++k) h[k] += lr * (fi[k] - pi[k]);
+    free(pi);
+    for (int i = 0; i < L; ++i)
+        for (int j = 0; j < L; ++j) {
+            if (i == j) continue;
+            int lo = i < j ? i : j, hi = i < j ? j : i;
+            size_t p = (size_t)lo * L - (size_t)lo * (lo - 1) / 2 + (size_t)(hi - lo);
+            for (int a = 0; a < q; ++a)
+                for (int b = 0; b < q; ++b) {
+                    int32_t c = (i < j) ? C[p * q * q + (size_t)a * q + b] : C[p * q * q + (size_t)b * q + a];
+                    J[jidx(L, q, i, j, a, b)] += lr * (fij[jidx(L, q, i, j, a, b)] - (double)c / M);
+                }
+        }
+}
+
+/* ------------------------------------------------------------------------
+ * Single-mutant library (Sec. 4.4): dE(i,a) = E(wt with s_i = a) - E(wt),
+ * computed by evaluating both energies by definition.  dE(i, wt_i) = 0.
+ * Output layout dE[i][a].
+ * ---------------------------------------------------------------------- */
+void orc_mutant_scan(const double *h, const double *J, int L, int q, const uint8_t *wt, double *dE)
+{
+    uint8_t *s = (uint8_t *)malloc((size_t)L);
+    double e0 = orc_energy(h, J, L, q, wt);
+    for (int i = 0; i < L; ++i)
+        for (int a = 0; a < q; ++a) {
+            memcpy(s, wt, (size_t)L);
+            s[i] = (uint8_t)a;
+            dE[(size_t)i * q + a] = (a == wt[i]) ? 0.0 : orc_energy(h, J, L, q, s) - e0;
+        }
+    free(s);
+}

@@ -1,0 +1,197 @@
+"""Pins of the oracle's statistics: chain counts, sequence weights (Eq. 3),
+weighted frequencies with pseudocount (Eqs. 2, 4-5), the Pearson check and
+the Boltzmann update (Eq. 9).
+
+References: numpy one-hot einsum counts, an O(N^2 L) numpy identity matrix,
+np.corrcoef, sum rules and closed-form special cases.
+"""
+import numpy as np
+import pytest
+
+from paper_2501_18456_gb300 import synth
+
+
+def onehot(S, q):
+    N, L = S.shape
+    X = np.zeros((N, L, q))
+    X[np.arange(N)[:, None], np.arange(L)[None, :], S] = 1.0
+    return X
+
+
+def full_counts_from_blocks(C, L, q, orc):
+    F = np.zeros((L, L, q, q), dtype=np.int64)
+    for i in range(L):
+        for j in range(i, L):
+            B = C[orc.block_index(L, i, j)]
+            F[i, j] = B
+            F[j, i] = B.T
+    return F
+
+
+def test_block_index_layout(orc):
+    L = 7
+    seen = []
+    for i in range(L):
+        for j in range(i, L):
+            seen.append(orc.block_index(L, i, j))
+    assert seen == list(range(orc.n_blocks(L)))
+
+
+@pytest.mark.parametrize("M,L,q", [(1, 1, 1), (57, 9, 5), (300, 6, 21)])
+def test_chain_stats_matches_einsum(orc, M, L, q):
+    S = synth.random_states(M, L, q, 7)
+    C = orc.chain_stats(S, q)
+    X = onehot(S, q)
+    ref = np.einsum("mia,mjb->ijab", X, X).astype(np.int64)
+    assert np.array_equal(full_counts_from_blocks(C, L, q, orc), ref)
+
+
+def test_chain_stats_sum_rules(orc):
+    M, L, q = 123, 8, 6
+    S = synth.random_states(M, L, q, 8)
+    C = orc.chain_stats(S, q).astype(np.int64)
+    F = full_counts_from_blocks(C, L, q, orc)
+    for i in range(L):
+        ci = np.diag(F[i, i])
+        assert ci.sum() == M
+        assert np.array_equal(F[i, i], np.diag(ci))  # off-diagonal of (i,i) is zero
+        for j in range(L):
+            assert np.array_equal(F[i, j].sum(axis=1), ci)
+
+
+def identity_matrix(S):
+    return (S[:, None, :] == S[None, :, :]).sum(axis=2)
+
+
+@pytest.mark.parametrize("N,L,seqid", [(1, 5, 0.8), (200, 40, 0.8), (150, 120, 0.8), (90, 33, 0.5)])
+def test_seq_weights_brute_force(orc, N, L, seqid):
+    S = synth.clustered_msa(N, L, 21, 3, n_ancestors=max(1, N // 8))
+    w, meff = orc.seq_weights(S, seqid)
+    ident = identity_matrix(S)
+    thr = orc.identity_threshold(seqid, L)
+    assert thr == int(np.ceil(seqid * L - 1e-9))
+    Nm = (ident >= thr).sum(axis=1)
+    assert np.allclose(w, 1.0 / Nm, rtol=0, atol=0)
+    assert meff == pytest.approx((1.0 / Nm).sum(), rel=1e-14)
+
+
+def test_identity_threshold_reading(orc):
+    # "identity >= 0.8 L": L = 256 -> 205 positions; L = 120 -> exactly 96
+    assert orc.identity_threshold(0.8, 256) == 205
+    assert orc.identity_threshold(0.8, 120) == 96
+    assert orc.identity_threshold(0.8, 5) == 4
+
+
+def test_seq_weights_special_cases(orc):
+    L = 30
+    same = np.tile(synth.random_states(1, L, 21, 1), (17, 1))
+    w, meff = orc.seq_weights(same)
+    assert np.allclose(w, 1 / 17) and meff == pytest.approx(1.0)
+    far = np.array([[k % 21] * L for k in range(21)], dtype=np.uint8)  # pairwise identity 0
+    w, meff = orc.seq_weights(far)
+    assert np.all(w == 1.0) and meff == 21.0
+
+
+def test_data_stats_matches_einsum(orc):
+    N, L, q = 400, 7, 5
+    S = synth.clustered_msa(N, L, q, 9, n_ancestors=40)
+    w = np.random.default_rng(2).uniform(0.1, 1.0, size=N)
+    alpha = 0.13
+    fi, fij = orc.data_stats(S, w, q, alpha)
+    X = onehot(S, q)
+    meff = w.sum()
+    f1 = np.einsum("m,mia->ia", w, X) / meff
+    f2 = np.einsum("m,mia,mjb->ijab", w, X, X) / meff
+    assert np.allclose(fi, (1 - alpha) * f1 + alpha / q, atol=1e-14)
+    for i in range(L):
+        for j in range(L):
+            if i == j:
+                assert np.allclose(fij[i, i], np.diag(fi[i]), atol=1e-14)
+            else:
+                assert np.allclose(fij[i, j], (1 - alpha) * f2[i, j] + alpha / q**2, atol=1e-14)
+
+
+def test_data_stats_pseudocount_limits_and_sum_rules(orc):
+    N, L, q = 100, 5, 4
+    S = synth.clustered_msa(N, L, q, 10, n_ancestors=10)
+    fi, fij = orc.data_stats(S, None, q, 1.0)
+    assert np.allclose(fi, 1 / q) and np.allclose(fij[0, 1], 1 / q**2)
+    fi, fij = orc.data_stats(S, None, q, 0.2)
+    assert np.allclose(fi.sum(axis=1), 1.0)
+    for i in range(L):
+        for j in range(L):
+            if i != j:
+                assert np.allclose(fij[i, j].sum(axis=1), fi[i], atol=1e-14)
+                assert np.allclose(fij[i, j], fij[j, i].T)
+    # alpha = 0, uniform weights: plain frequencies
+    fi0, _ = orc.data_stats(S, None, q, 0.0)
+    assert np.allclose(fi0, onehot(S, q).mean(axis=0))
+
+
+def connected(fi, fij):
+    L, q = fi.shape
+    xs = []
+    for i in range(L):
+        for j in range(i + 1, L):
+            xs.append((fij[i, j] - np.outer(fi[i], fi[j])).ravel())
+    return np.concatenate(xs)
+
+
+def test_pearson_matches_corrcoef(orc):
+    N, L, q, M = 300, 8, 5, 250
+    data = synth.clustered_msa(N, L, q, 11, n_ancestors=30)
+    fi, fij = orc.data_stats(data, None, q, 0.05)
+    S = synth.random_states(M, L, q, 12)
+    C = orc.chain_stats(S, q)
+    rho = orc.pearson(fi, fij, C, M)
+    X = onehot(S, q)
+    p1 = X.mean(axis=0)
+    p2 = np.einsum("mia,mjb->ijab", X, X) / M
+    want = np.corrcoef(connected(fi, fij), connected(p1, p2))[0, 1]
+    assert rho == pytest.approx(want, abs=1e-12)
+
+
+def test_pearson_identical_statistics_is_one(orc):
+    M, L, q = 500, 6, 4
+    S = synth.clustered_msa(M, L, q, 13, n_ancestors=20)
+    fi, fij = orc.data_stats(S, None, q, 0.0)  # exact chain frequencies
+    rho = orc.pearson(fi, fij, orc.chain_stats(S, q), M)
+    assert rho == pytest.approx(1.0, abs=1e-12)
+
+
+def test_update_closed_form_and_symmetry(orc):
+    N, L, q, M = 200, 6, 5, 150
+    rng = np.random.default_rng(4)
+    h = rng.normal(size=(L, q))
+    J = np.zeros((L, L, q, q))
+    for i in range(L):
+        for j in range(i + 1, L):
+            B = rng.normal(size=(q, q))
+            J[i, j], J[j, i] = B, B.T
+    fi, fij = orc.data_stats(synth.clustered_msa(N, L, q, 14, n_ancestors=20), None, q, 0.1)
+    S = synth.random_states(M, L, q, 15)
+    C = orc.chain_stats(S, q)
+    lr = 0.05
+    h2, J2 = orc.update(h, J, fi, fij, C, M, lr)
+    X = onehot(S, q)
+    p1 = X.mean(axis=0)
+    p2 = np.einsum("mia,mjb->ijab", X, X) / M
+    assert np.allclose(h2, h + lr * (fi - p1), atol=1e-14)
+    for i in range(L):
+        for j in range(L):
+            if i == j:
+                assert np.all(J2[i, i] == 0)
+            else:
+                assert np.allclose(J2[i, j], J[i, j] + lr * (fij[i, j] - p2[i, j]), atol=1e-14)
+    assert np.array_equal(J2, J2.transpose(1, 0, 3, 2))
+
+
+def test_update_fixed_point(orc):
+    """f = p leaves the parameters unchanged (Eq. 9 at convergence)."""
+    M, L, q = 64, 5, 3
+    S = synth.random_states(M, L, q, 16)
+    fi, fij = orc.data_stats(S, None, q, 0.0)
+    h = np.random.default_rng(1).normal(size=(L, q))
+    J = np.zeros((L, L, q, q))
+    h2, J2 = orc.update(h, J, fi, fij, orc.chain_stats(S, q), M, 0.3)
+    assert np.allclose(h2, h, atol=1e-15) and np.allclose(J2, 0, atol=1e-15)
