@@ -1,0 +1,229 @@
+/*
+ * bmdca.h -- C ABI of libbmdca.so, the GB300 (sm_103a) hot path of
+ * Boltzmann-machine Direct Coupling Analysis (bmDCA) as described in
+ * adabmDCA 2.0 (Muntoni, Pagnani, Weigt, Zamponi et al., arXiv 2501.18456).
+ *
+ * Model (Sec. 2.1, Eq. 1): a Potts model over L sites and q symbols,
+ *     p(s) = exp(-E(s)) / Z,
+ *     E(s) = - sum_i h_i(s_i) - sum_{i<j} J_ij(s_i, s_j),
+ * with J_ij(a,b) = J_ji(b,a) and J_ii = 0.  Symbol 0 is the alignment gap
+ * (Sec. 2.3, Table 1).
+ *
+ * Common conventions for every entry point:
+ *   - Layouts are C row-major.  h is float[L][q]; J is float[L][L][q][q]
+ *     with J[i][j][a][b] = J_ij(a,b).  Sequences and chain states are
+ *     uint8[n][L], every symbol < q.
+ *   - Pair counts use the upper block triangle: for i <= j the q x q block
+ *     (i,j) sits at block index i*L - i*(i-1)/2 + (j-i) and holds
+ *     C[a][b] = #{chains m : s_i = a, s_j = b}.  There are L*(L+1)/2
+ *     blocks; the diagonal block (i,i) carries the single-site counts on
+ *     its diagonal.
+ *   - `where` arguments: BM_HOST (0) for a host pointer, BM_DEVICE (1) for
+ *     a device pointer on the current device.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call is stream-ordered and asynchronous, except the
+ *     ones that return a host scalar (they synchronise the stream) and the
+ *     ones that copy from/to pageable host memory.
+ *   - The caller owns every raw buffer it passes.  The library owns the
+ *     internals of bm_model / bm_chains handles (device memory included)
+ *     until the matching *_free call.
+ *   - Return value: BM_OK or a negative bm_status.  No exception crosses
+ *     the ABI.  bm_last_error() returns a message for the calling thread's
+ *     last failure.  Invalid arguments are rejected before any GPU work.
+ *   - Limits: 1 <= q <= 32, 1 <= L <= 4096, M >= 1.
+ *   - Handles are not thread-safe: one host thread at a time per handle.
+ *
+ * Random numbers: every draw uses Philox4x64-10 (Salmon et al., SC'11) with
+ * key (seed, 0) and counter (chain, sweep, site, tag), tag 0 for Gibbs
+ * draws and tag 1 for chain initialisation; the uniform is the top 24 bits
+ * of output word 0 scaled by 2^-24.  Results therefore depend only on the
+ * seed and the global chain / sweep / site indices, not on launch shapes.
+ */
+#ifndef BMDCA_H
+#define BMDCA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bm_model_s *bm_model;    /* device h, J and derived layouts */
+typedef struct bm_chains_s *bm_chains;  /* device chain states + seed + sweep counter */
+
+typedef enum {
+    BM_OK = 0,
+    BM_EINVAL = -1,    /* bad argument, shape, symbol or asymmetric J */
+    BM_ENOMEM = -2,    /* device allocation failed */
+    BM_ECUDA = -3,     /* a CUDA runtime call failed (message has the name) */
+    BM_ENUMERIC = -4,  /* NaN/Inf in parameters */
+    BM_ETIMEOUT = -5,  /* a bounded device-side wait gave up */
+    BM_EDEVICE = -6,   /* a device-side check recorded an error */
+    BM_EBUSY = -7      /* resource in use */
+} bm_status;
+
+enum { BM_HOST = 0, BM_DEVICE = 1 };
+
+/* Which kernel form bm_gibbs_sweep uses (bm_model_set_engine). */
+enum {
+    BM_ENGINE_SIMT = 0,  /* FP32 CUDA-core gather of J rows (default) */
+    BM_ENGINE_AUTO = 1   /* library picks the fastest form with FP32-class fields */
+};
+
+/* Library version string, e.g. "bmdca-gb300 0.1". */
+const char *bm_version(void);
+
+/* Message for the calling thread's most recent failure ("" if none). */
+const char *bm_last_error(void);
+
+/*
+ * bm_potts_load -- upload a Potts model (Eq. 1) and build its device layouts.
+ *   h     : float[L][q] fields.
+ *   J     : float[L][L][q][q] couplings, J[i][j][a][b] = J_ij(a,b).
+ *   where : BM_HOST or BM_DEVICE for both h and J (copied, not retained).
+ * Checks (BM_EINVAL): L, q in range; J exactly symmetric
+ * (J[i][j][a][b] == J[j][i][b][a]); J[i][i] == 0.  NaN/Inf -> BM_ENUMERIC.
+ * Synchronises `stream` (the checks are read back).  *out receives the
+ * handle on success.
+ */
+int bm_potts_load(const float *h, const float *J, int L, int q, int where, void *stream,
+                  bm_model *out);
+
+/* Release a model and its device memory.  NULL is accepted. */
+int bm_potts_free(bm_model m);
+
+/* Copy the current parameters (after any bm_update) to h / J (either may be
+ * NULL), same layouts as bm_potts_load.  Stream-ordered. */
+int bm_potts_get(bm_model m, float *h, float *J, int where, void *stream);
+
+/* Overwrite the live parameters of m in place from h / J (either may be
+ * NULL; same layouts as bm_potts_load).  No symmetry or finiteness check:
+ * the caller guarantees the invariants bm_potts_load verifies (use it for
+ * parameters that came out of this library, e.g. a checkpoint).  Allocates
+ * nothing; stream-ordered. */
+int bm_potts_set(bm_model m, const float *h, const float *J, int where, void *stream);
+
+/* L and q of a model. */
+int bm_potts_shape(bm_model m, int *L, int *q);
+
+/*
+ * bm_chains_init -- create M persistent chains (Sec. 2.1, PCD) for model m.
+ *   init_or_null : uint8[M][L] start states (`where` says host/device), or
+ *                  NULL for uniformly random states: symbol of chain m at
+ *                  site i = floor(u24 * q / 2^24), u24 from Philox counter
+ *                  (m, 0, i, 1).
+ *   seed         : Philox key word 0 for every later draw of these chains.
+ * The sweep counter starts at 0.  Symbols >= q in init -> BM_EINVAL
+ * (checked on the device; the call synchronises `stream`).
+ */
+int bm_chains_init(bm_model m, int M, uint64_t seed, const uint8_t *init_or_null, int where,
+                   void *stream, bm_chains *out);
+
+/* Release chains.  NULL is accepted. */
+int bm_chains_free(bm_chains c);
+
+/* Copy the chain states (uint8[M][L]) to dst.  Stream-ordered. */
+int bm_chains_get(bm_chains c, uint8_t *dst, int where, void *stream);
+
+/* Overwrite the chain states from src (uint8[M][L]); the sweep counter is
+ * left unchanged.  Symbols are not re-checked (caller guarantees < q). */
+int bm_chains_set(bm_chains c, const uint8_t *src, int where, void *stream);
+
+/* Read / set the global sweep counter (the Philox `sweep` word of the next
+ * sweep).  Setting it lets a caller replay or resume a run bit-identically. */
+int bm_chains_sweep_counter(bm_chains c, uint64_t *sweep);
+int bm_chains_set_sweep_counter(bm_chains c, uint64_t sweep);
+int bm_chains_shape(bm_chains c, int *M, int *L);
+
+/*
+ * bm_gibbs_sweep -- nsweeps persistent-chain Gibbs sweeps (Sec. 2.1,
+ * "Monte Carlo estimation of the gradient"; a sweep proposes every site
+ * once, Sec. 3.4).  Sites are visited in order i = 0..L-1.  For chain m
+ * and site i the local field H_i(a) = h_i(a) + sum_{j != i} J_ij(a, s_j) is
+ * formed from the current states, and s_i is drawn from p(a) ~
+ * exp(beta * H_i(a)) by inverse CDF (first a with u * S_total < S_a over
+ * prefix sums in a ascending, weights exp(beta*H_a - max_b beta*H_b)) with
+ * u from Philox counter (m, sweep, i, 0).  The sweep counter advances by
+ * nsweeps.  beta = 1 for training; beta != 1 samples p ~ exp(-beta E)
+ * (Sec. 4.1 sampling at inverse temperature).  nsweeps >= 0, beta finite.
+ */
+int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *stream);
+
+/* Select the kernel form used by bm_gibbs_sweep for this model
+ * (BM_ENGINE_*).  BM_EINVAL for an unknown engine. */
+int bm_model_set_engine(bm_model m, int engine);
+
+/*
+ * bm_chain_stats -- model statistics from the chains (Sec. 2.1: p_i, p_ij
+ * estimated as chain frequencies).  Writes int32 counts in the upper
+ * block-triangle layout above to counts_dev (device, L*(L+1)/2*q*q
+ * int32, fully overwritten).  p = count / M.  Exact (integer).
+ */
+int bm_chain_stats(bm_chains c, int32_t *counts_dev, void *stream);
+
+/*
+ * bm_seq_weights -- importance weights, Eq. 3: w_m = 1 / N_m where N_m is
+ * the number of sequences n (m included) whose identity with m -- number
+ * of positions with equal symbols, gap included -- is >= ceil(seqid * L)
+ * (the ceiling taken after subtracting 1e-9, so seqid = 0.8, L = 120 gives
+ * 96).  msa_dev: device uint8[N][L]; w_dev: device float[N];
+ * meff_host (may be NULL): M_eff = sum_m w_m in FP64 (Sec. 3.4), returned
+ * after synchronising `stream`.  0 < seqid <= 1.
+ */
+int bm_seq_weights(const uint8_t *msa_dev, int N, int L, double seqid, float *w_dev,
+                   double *meff_host, void *stream);
+
+/*
+ * bm_data_stats -- empirical frequencies, Eq. 2, with the pseudocount of
+ * Eqs. 4-5:  f_i = (1-alpha) f_i^data + alpha/q,
+ *            f_ij = (1-alpha) f_ij^data + alpha/q^2   (i != j),
+ * f^data weighted by w (w_or_null == NULL: uniform weights) and divided by
+ * M_eff = sum w.  pseudocount < 0 selects the paper's default alpha =
+ * 1/M_eff (Sec. 3.4).  Outputs (device): fi_dev float[L][q], fij_dev
+ * float[L][L][q][q] (diagonal blocks: fij[i][i][a][b] = delta_ab f_i(a)).
+ * Weighted sums are accumulated exactly in 64-bit fixed point (2^-40
+ * resolution per weight), so the result is deterministic.
+ */
+int bm_data_stats(const uint8_t *msa_dev, const float *w_or_null, int N, int L, int q,
+                  double pseudocount, float *fi_dev, float *fij_dev, void *stream);
+
+/*
+ * bm_update -- one Boltzmann-learning step, Eq. 9:
+ *     h_i(a)    += lr (f_i(a)    - p_i(a)),
+ *     J_ij(a,b) += lr (f_ij(a,b) - p_ij(a,b))   (i != j; J_ii stays 0),
+ * with p = counts / M (counts from bm_chain_stats, device) and f from
+ * bm_data_stats (device).  In the same pass the Pearson correlation of the
+ * connected correlations C^data = f_ij - f_i f_j and C^model = p_ij - p_i p_j
+ * over i < j and all (a,b) is reduced in FP64 (Sec. 2.1, convergence
+ * criterium).
+ *   pearson_out == NULL : no Pearson, update applied, fully asynchronous.
+ *   pearson_out != NULL : synchronises `stream`; *pearson_out = rho of the
+ *                         statistics passed in (the parameters that
+ *                         produced the chains); the update is applied only
+ *                         if rho < target (pass target > 1 to always apply).
+ *   applied_out (may be NULL) receives 1 if the parameters changed.
+ */
+int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int32_t *counts,
+              int M, float lr, double target, double *pearson_out, int *applied_out,
+              void *stream);
+
+/*
+ * bm_energy_score -- DCA energy E(s) of n sequences (Eq. 1; Sec. 4.3: low
+ * energy = good sequence).  seqs_dev: device uint8[n][L]; E_dev: device
+ * float[n].  FP32 accumulation.
+ */
+int bm_energy_score(bm_model m, const uint8_t *seqs_dev, int n, float *E_dev, void *stream);
+
+/*
+ * bm_mutant_scan -- single-mutant library (Sec. 4.4): dE[i][a] =
+ * E(wt with s_i = a) - E(wt) = -(H_i(a) - H_i(wt_i)) with H the local
+ * field at the wild type; dE[i][wt_i] = 0.  wt: uint8[L] (`where`);
+ * dE_dev: device float[L][q].
+ */
+int bm_mutant_scan(bm_model m, const uint8_t *wt, int where, float *dE_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BMDCA_H */

@@ -1,0 +1,118 @@
+// Internal declarations shared by the translation units of libbmdca.so.
+// Nothing here is part of the public ABI (include/bmdca.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/bmdca.h"
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+struct bm_model_s {
+    int L = 0, q = 0;
+    int device = 0;
+    int engine = BM_ENGINE_SIMT;
+    // Parameters: front buffer is the live model, back buffer receives the
+    // next iterate of bm_update (swapped in when the update is applied).
+    float *h = nullptr, *J = nullptr;
+    float *h_back = nullptr, *J_back = nullptr;
+    // Small device scratch for flags / reductions (owned).
+    int *dflags = nullptr;       // [8] error / check words
+    double *dred = nullptr;      // reduction partials, capacity red_cap doubles
+    size_t red_cap = 0;
+    int num_sms = 0;
+};
+
+struct bm_chains_s {
+    int M = 0, L = 0, q = 0;
+    int device = 0;
+    uint8_t *s = nullptr;  // [M][L]
+    uint64_t seed = 0;
+    uint64_t sweep = 0;    // Philox sweep word of the next sweep
+};
+
+// ---------------------------------------------------------------------------
+// Errors (thread-local message, see bm_last_error)
+// ---------------------------------------------------------------------------
+int bm_fail(int code, const char *fmt, ...);
+int bm_cuda_fail(cudaError_t e, const char *what);
+
+#define BM_CK(call)                                              \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return bm_cuda_fail(e_, #call);   \
+    } while (0)
+
+#define BM_CK_LAUNCH(name)                                       \
+    do {                                                         \
+        cudaError_t e_ = cudaGetLastError();                     \
+        if (e_ != cudaSuccess) return bm_cuda_fail(e_, name);    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11): key (seed, 0), counter
+// (chain, sweep, site, tag); only output word 0 is needed by the draws.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t bm_philox_word0(uint64_t seed, uint64_t c0, uint64_t c1,
+                                                    uint64_t c2, uint64_t c3)
+{
+    const uint64_t kM0 = 0xD2E7470EE14C6C93ULL, kM1 = 0xCA5A826395121157ULL;
+    const uint64_t kW0 = 0x9E3779B97F4A7C15ULL, kW1 = 0xBB67AE8584CAA73BULL;
+    uint64_t k0 = seed, k1 = 0;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0hi = __umul64hi(kM0, c0), p0lo = kM0 * c0;
+        const uint64_t p1hi = __umul64hi(kM1, c2), p1lo = kM1 * c2;
+        const uint64_t x0 = p1hi ^ c1 ^ k0;
+        const uint64_t x2 = p0hi ^ c3 ^ k1;
+        c0 = x0;
+        c1 = p1lo;
+        c2 = x2;
+        c3 = p0lo;
+        k0 += kW0;
+        k1 += kW1;
+    }
+    return c0;
+}
+
+// 24-bit uniform numerator of a draw (top 24 bits of word 0).
+__device__ __forceinline__ uint32_t bm_u24(uint64_t seed, uint64_t chain, uint64_t sweep,
+                                           uint64_t site, uint64_t tag)
+{
+    return (uint32_t)(bm_philox_word0(seed, chain, sweep, site, tag) >> 40);
+}
+
+// Index of the upper-triangle pair block (i <= j).
+__host__ __device__ __forceinline__ size_t bm_pair_block(int L, int i, int j)
+{
+    return (size_t)i * L - (size_t)i * (i - 1) / 2 + (size_t)(j - i);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (each returns BM_OK or an error code)
+// ---------------------------------------------------------------------------
+int bm_launch_check_model(const float *h, const float *J, int L, int q, int *dflags,
+                          cudaStream_t st);
+int bm_launch_check_symbols(const uint8_t *s, size_t n, int q, int *dflag, cudaStream_t st);
+int bm_launch_chains_init(uint8_t *s, int M, int L, int q, uint64_t seed, cudaStream_t st);
+int bm_launch_gibbs_simt(const bm_model_s *m, bm_chains_s *c, int nsweeps, float beta,
+                         cudaStream_t st);
+int bm_launch_chain_stats(const uint8_t *s, int M, int L, int q, int32_t *counts,
+                          cudaStream_t st);
+int bm_launch_seq_weights(const uint8_t *msa, int N, int L, int thr, float *w, int *cnt,
+                          double *meff_dev, cudaStream_t st);
+int bm_launch_data_stats(const uint8_t *msa, const float *w, int N, int L, int q, double alpha,
+                         int frac_bits, double meff, float *fi, float *fij,
+                         unsigned long long *acc_fi, cudaStream_t st);
+int bm_launch_weight_sum(const float *w, int N, double *out2, cudaStream_t st);
+int bm_launch_update(bm_model_s *m, const float *fi, const float *fij, const int32_t *counts,
+                     int M, float lr, int want_pearson, double *partials, int nparts,
+                     double *moments, cudaStream_t st);
+int bm_update_num_partials(int L);
+int bm_launch_energy(const float *h, const float *J, int L, int q, const uint8_t *seqs, int n,
+                     float *E, cudaStream_t st);
+int bm_launch_mutant_scan(const float *h, const float *J, int L, int q, const uint8_t *wt,
+                          float *dE, cudaStream_t st);

@@ -1,0 +1,130 @@
+// Model checks, energy scoring (Sec. 4.3) and single-mutant scans (Sec. 4.4).
+#include "bm_internal.cuh"
+
+#include <algorithm>
+
+namespace {
+
+// Flags: bit 0 asymmetric J, bit 1 nonzero J_ii, bit 2 non-finite value.
+__global__ void k_check_model(const float *__restrict__ h, const float *__restrict__ J, int L,
+                              int q, int *flags)
+{
+    const size_t n = (size_t)L * L * q * q;
+    const size_t qq = (size_t)q * q;
+    int f = 0;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t blk = t / qq, e = t % qq;
+        const int i = (int)(blk / L), j = (int)(blk % L);
+        const int a = (int)(e / q), b = (int)(e % q);
+        const float v = J[t];
+        if (!isfinite(v)) f |= 4;
+        if (i == j) {
+            if (v != 0.0f) f |= 2;
+        } else if (i < j) {
+            const float w = J[(((size_t)j * L + i) * q + b) * q + a];
+            if (!(v == w) && isfinite(v) && isfinite(w)) f |= 1;
+        }
+        if (t < (size_t)L * q && !isfinite(h[t])) f |= 4;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+__global__ void k_check_symbols(const uint8_t *__restrict__ s, size_t n, int q, int *flag)
+{
+    int bad = 0;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (size_t)gridDim.x * blockDim.x)
+        bad |= (s[t] >= q);
+    if (bad) atomicOr(flag, 1);
+}
+
+// Energy E(s) = -sum_i h_i(s_i) - sum_{i<j} J_ij(s_i, s_j): one warp per
+// sequence, lanes stride over j for each i; FP32 accumulation, warp sum.
+__global__ void __launch_bounds__(256) k_energy(const float *__restrict__ h,
+                                                const float *__restrict__ J, int L, int q,
+                                                const uint8_t *__restrict__ S, int n,
+                                                float *__restrict__ E)
+{
+    extern __shared__ uint8_t sst[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    uint8_t *s = sst + (size_t)warp * L;
+    const size_t qq = (size_t)q * q;
+    for (long long k = (long long)blockIdx.x * nw + warp; k < n; k += (long long)gridDim.x * nw) {
+        for (int t = lane; t < L; t += 32) s[t] = S[(size_t)k * L + t];
+        __syncwarp();
+        float acc = 0.0f;
+        for (int i = 0; i < L; ++i) {
+            const int si = s[i];
+            if (lane == 0) acc -= h[(size_t)i * q + si];
+            const float *row = J + ((size_t)i * L) * qq + (size_t)si * q;
+            for (int j = i + 1 + lane; j < L; j += 32) acc -= __ldg(row + (size_t)j * qq + s[j]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) E[k] = acc;
+        __syncwarp();
+    }
+}
+
+// dE(i,a) = -(H_i(a) - H_i(wt_i)), H_i(a) = h_i(a) + sum_{j != i} J_ij(a, wt_j):
+// one warp per site, lane = a; J_ij(a, b) read as the contiguous row
+// J[j][i][b][.] (symmetry), the j = i term is an exact zero.
+__global__ void k_mutant_scan(const float *__restrict__ h, const float *__restrict__ J, int L,
+                              int q, const uint8_t *__restrict__ wt, float *__restrict__ dE)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= L) return;
+    const int i = warp;
+    const int aa = lane < q ? lane : q - 1;
+    const size_t qq = (size_t)q * q;
+    float H = h[(size_t)i * q + aa];
+    for (int j = 0; j < L; ++j) H += __ldg(J + ((size_t)j * L + i) * qq + (size_t)wt[j] * q + aa);
+    const float Hw = __shfl_sync(0xffffffffu, H, wt[i]);
+    if (lane < q) dE[(size_t)i * q + lane] = (lane == wt[i]) ? 0.0f : -(H - Hw);
+}
+
+}  // namespace
+
+int bm_launch_check_model(const float *h, const float *J, int L, int q, int *dflags,
+                          cudaStream_t st)
+{
+    BM_CK(cudaMemsetAsync(dflags, 0, sizeof(int), st));
+    const size_t n = (size_t)L * L * q * q;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+    k_check_model<<<std::max(grid, 1), 256, 0, st>>>(h, J, L, q, dflags);
+    BM_CK_LAUNCH("k_check_model");
+    return BM_OK;
+}
+
+int bm_launch_check_symbols(const uint8_t *s, size_t n, int q, int *dflag, cudaStream_t st)
+{
+    BM_CK(cudaMemsetAsync(dflag, 0, sizeof(int), st));
+    if (n == 0) return BM_OK;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+    k_check_symbols<<<grid, 256, 0, st>>>(s, n, q, dflag);
+    BM_CK_LAUNCH("k_check_symbols");
+    return BM_OK;
+}
+
+int bm_launch_energy(const float *h, const float *J, int L, int q, const uint8_t *seqs, int n,
+                     float *E, cudaStream_t st)
+{
+    if (n == 0) return BM_OK;
+    const int warps = 8;
+    const int grid = (int)std::min<long long>(((long long)n + warps - 1) / warps, 152LL * 16);
+    k_energy<<<grid, warps * 32, (size_t)warps * L, st>>>(h, J, L, q, seqs, n, E);
+    BM_CK_LAUNCH("k_energy");
+    return BM_OK;
+}
+
+int bm_launch_mutant_scan(const float *h, const float *J, int L, int q, const uint8_t *wt,
+                          float *dE, cudaStream_t st)
+{
+    const int threads = 256;
+    const int grid = (L * 32 + threads - 1) / threads;
+    k_mutant_scan<<<grid, threads, 0, st>>>(h, J, L, q, wt, dE);
+    BM_CK_LAUNCH("k_mutant_scan");
+    return BM_OK;
+}

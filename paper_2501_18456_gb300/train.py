@@ -1,0 +1,89 @@
+"""Host-side bmDCA training loop (adabmDCA 2.0, Sec. 2.1 and Sec. 3).
+
+Every step runs in libbmdca.so kernels; this module only sequences the C
+entry points:
+
+  preprocessing (once):  bm_seq_weights (Eq. 3) -> bm_data_stats (Eqs. 2, 4-5)
+  per iteration t:       bm_gibbs_sweep x nsweeps (PCD chains, theta_t)
+                         -> bm_chain_stats -> bm_update: Pearson of the
+                         connected correlations of theta_t's chains; stop if
+                         rho >= target (theta_t kept), else Eq. 9 -> theta_{t+1}
+
+Initial parameters are the caller's choice.  `profile_init` offers the
+independent-site model h_i(a) = log f_i(a), J = 0 (finite thanks to the
+pseudocount); it is a one-off element-wise log of L*q numbers done with torch
+before training starts, outside the hot path.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import torch
+
+from . import bmdca
+
+
+@dataclasses.dataclass
+class TrainConfig:
+    M: int = 10000          # persistent chains (paper default, Sec. 3.4)
+    nsweeps: int = 10       # sweeps per update (Sec. 3.4)
+    lr: float = 0.01        # learning rate; set explicitly by every workload
+    max_iters: int = 500
+    target: float = 0.95    # Pearson target (Sec. 2.1)
+    seed: int = 0
+    seqid: float = 0.8      # identity threshold of Eq. 3
+    pseudocount: float = -1.0  # < 0: 1 / M_eff (Sec. 3.4)
+    reweight: bool = True
+
+
+@dataclasses.dataclass
+class DataStats:
+    fi: torch.Tensor
+    fij: torch.Tensor
+    meff: float
+    weights: torch.Tensor | None
+
+
+def data_statistics(msa: torch.Tensor, q: int, cfg: TrainConfig, stream=None) -> DataStats:
+    """Weights (if enabled) and pseudocounted frequencies of a device MSA."""
+    N, L = msa.shape
+    w = None
+    meff = float(N)
+    if cfg.reweight:
+        w = torch.empty(N, dtype=torch.float32, device=msa.device)
+        meff = bmdca.bm_seq_weights(msa, w, cfg.seqid, True, stream)
+    fi = torch.empty((L, q), dtype=torch.float32, device=msa.device)
+    fij = torch.empty((L, L, q, q), dtype=torch.float32, device=msa.device)
+    bmdca.bm_data_stats(msa, w, q, cfg.pseudocount, fi, fij, stream)
+    return DataStats(fi, fij, meff, w)
+
+
+def profile_init(stats: DataStats):
+    """Initial model: h_i(a) = log f_i(a), J = 0 (device tensors)."""
+    L, q = stats.fi.shape
+    h = torch.log(stats.fi)
+    J = torch.zeros((L, L, q, q), dtype=torch.float32, device=stats.fi.device)
+    return h, J
+
+
+def train(model: bmdca.Model, chains: bmdca.Chains, stats: DataStats, cfg: TrainConfig,
+          log=None, stream=None):
+    """Run up to cfg.max_iters iterations; returns the list of per-iteration records."""
+    L, q = model.L, model.q
+    counts = torch.empty((bmdca.n_blocks(L), q, q), dtype=torch.int32, device=stats.fi.device)
+    history = []
+    for it in range(cfg.max_iters):
+        t0 = time.perf_counter()
+        bmdca.bm_gibbs_sweep(model, chains, cfg.nsweeps, 1.0, stream)
+        bmdca.bm_chain_stats(chains, counts, stream)
+        rho, applied = bmdca.bm_update(model, stats.fi, stats.fij, counts, chains.M, cfg.lr,
+                                       cfg.target, True, stream)
+        rec = {"iteration": it, "pearson": rho, "applied": applied,
+               "seconds": time.perf_counter() - t0}
+        history.append(rec)
+        if log is not None:
+            log(rec)
+        if not applied:
+            break
+    return history
