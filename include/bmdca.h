@@ -103,6 +103,12 @@ int bm_potts_get(bm_model m, float *h, float *J, int where, void *stream);
  * nothing; stream-ordered. */
 int bm_potts_set(bm_model m, const float *h, const float *J, int where, void *stream);
 
+/* Synchronise `stream` and report device-side errors recorded by earlier
+ * kernels of this model (bounded waits that gave up): BM_OK, or
+ * BM_ETIMEOUT (the error word is then cleared).  bm_update with a Pearson
+ * request performs the same check. */
+int bm_device_status(bm_model m, void *stream);
+
 /* L and q of a model. */
 int bm_potts_shape(bm_model m, int *L, int *q);
 
@@ -138,7 +144,7 @@ int bm_chains_shape(bm_chains c, int *M, int *L);
 /*
  * bm_gibbs_sweep -- nsweeps persistent-chain Gibbs sweeps (Sec. 2.1,
  * "Monte Carlo estimation of the gradient"; a sweep proposes every site
- * once, Sec. 3.4).  Sites are visited in order i = 0..L-1.  For chain m
+ * once, Sec. 3.3).  Sites are visited in order i = 0..L-1.  For chain m
  * and site i the local field H_i(a) = h_i(a) + sum_{j != i} J_ij(a, s_j) is
  * formed from the current states, and s_i is drawn from p(a) ~
  * exp(beta * H_i(a)) by inverse CDF (first a with u * S_total < S_a over
@@ -162,24 +168,24 @@ int bm_model_set_engine(bm_model m, int engine);
 int bm_chain_stats(bm_chains c, int32_t *counts_dev, void *stream);
 
 /*
- * bm_seq_weights -- importance weights, Eq. 3: w_m = 1 / N_m where N_m is
+ * bm_seq_weights -- importance weights, Eq. 7: w_m = 1 / N_m where N_m is
  * the number of sequences n (m included) whose identity with m -- number
  * of positions with equal symbols, gap included -- is >= ceil(seqid * L)
  * (the ceiling taken after subtracting 1e-9, so seqid = 0.8, L = 120 gives
  * 96).  msa_dev: device uint8[N][L]; w_dev: device float[N];
- * meff_host (may be NULL): M_eff = sum_m w_m in FP64 (Sec. 3.4), returned
+ * meff_host (may be NULL): M_eff = sum_m w_m in FP64 (Sec. 3.3), returned
  * after synchronising `stream`.  0 < seqid <= 1.
  */
 int bm_seq_weights(const uint8_t *msa_dev, int N, int L, double seqid, float *w_dev,
                    double *meff_host, void *stream);
 
 /*
- * bm_data_stats -- empirical frequencies, Eq. 2, with the pseudocount of
- * Eqs. 4-5:  f_i = (1-alpha) f_i^data + alpha/q,
+ * bm_data_stats -- empirical frequencies, Eq. 3, with the pseudocount of
+ * Eqs. 8-9:  f_i = (1-alpha) f_i^data + alpha/q,
  *            f_ij = (1-alpha) f_ij^data + alpha/q^2   (i != j),
  * f^data weighted by w (w_or_null == NULL: uniform weights) and divided by
  * M_eff = sum w.  pseudocount < 0 selects the paper's default alpha =
- * 1/M_eff (Sec. 3.4).  Outputs (device): fi_dev float[L][q], fij_dev
+ * 1/M_eff (Sec. 3.3).  Outputs (device): fi_dev float[L][q], fij_dev
  * float[L][L][q][q] (diagonal blocks: fij[i][i][a][b] = delta_ab f_i(a)).
  * Weighted sums are accumulated exactly in 64-bit fixed point (2^-40
  * resolution per weight), so the result is deterministic.
@@ -188,7 +194,7 @@ int bm_data_stats(const uint8_t *msa_dev, const float *w_or_null, int N, int L, 
                   double pseudocount, float *fi_dev, float *fij_dev, void *stream);
 
 /*
- * bm_update -- one Boltzmann-learning step, Eq. 9:
+ * bm_update -- one Boltzmann-learning step, Eq. 5:
  *     h_i(a)    += lr (f_i(a)    - p_i(a)),
  *     J_ij(a,b) += lr (f_ij(a,b) - p_ij(a,b))   (i != j; J_ii stays 0),
  * with p = counts / M (counts from bm_chain_stats, device) and f from

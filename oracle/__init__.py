@@ -14,12 +14,12 @@ in the C file; in short:
   chains_init ............. Sec. 2.1 (uniform random chains)
   energy .................. Eq. 1
   fields / conditional .... Eq. 1 with all but one site fixed
-  gibbs / gibbs_verify .... Sec. 2.1 (PCD Gibbs sweeps), Sec. 3.4 (sweep)
+  gibbs / gibbs_verify .... Sec. 2.1 (PCD Gibbs sweeps), Sec. 3.3 (sweep)
   chain_stats ............. Sec. 2.1 (p_i, p_ij from the chains)
-  seq_weights ............. Eq. 3 (80% identity weights), M_eff Sec. 3.4
-  data_stats .............. Eq. 2 + pseudocount Eqs. 4-5
+  seq_weights ............. Eq. 7 (80% identity weights), M_eff Sec. 3.3
+  data_stats .............. Eq. 3 + pseudocount Eqs. 8-9
   pearson ................. Sec. 2.1 "Convergence criterium"
-  update .................. Eq. 9 (Boltzmann learning step)
+  update .................. Eq. 5 (Boltzmann learning step)
   mutant_scan ............. Sec. 4.4 (single-mutant dE)
 
 Parity status of every function is "pinned" (see the CPU tests).
@@ -203,7 +203,7 @@ def chain_stats(states, q: int) -> np.ndarray:
 
 
 def identity_threshold(seqid: float, L: int) -> int:
-    """Smallest integer identity count that is >= seqid * L (Eq. 3 reading)."""
+    """Smallest integer identity count that is >= seqid * L (Eq. 7 reading)."""
     return int(math.ceil(seqid * L - 1e-9))
 
 

@@ -174,7 +174,7 @@ void orc_conditional(const double *h, const double *J, int L, int q, const uint8
 
 /* ------------------------------------------------------------------------
  * Persistent-chain Gibbs sampling (Sec. 2.1, "Monte Carlo estimation of
- * the gradient"; a sweep proposes every site once, Sec. 3.4 "Number of
+ * the gradient"; a sweep proposes every site once, Sec. 3.3 "Number of
  * Monte Carlo steps").  Reading: sites visited in order 0..L-1 every sweep;
  * sweep counter = sweep0 + k, never repeated over a run.
  * ---------------------------------------------------------------------- */
@@ -254,11 +254,11 @@ void orc_chain_stats(const uint8_t *S, int M, int L, int q, int32_t *C)
 }
 
 /* ------------------------------------------------------------------------
- * Importance weights, Eq. 3 (Sec. 2.3): w_m = 1 / N_m with N_m the number
+ * Importance weights, Eq. 7 (Sec. 2.3): w_m = 1 / N_m with N_m the number
  * of sequences n (m itself included) whose identity with m -- the count of
  * positions with equal symbols, gaps included -- is at least thr.
  * The caller passes the integer threshold thr = ceil(seqid * L).
- * M_eff = sum_m w_m (Sec. 3.4, "Regularization").
+ * M_eff = sum_m w_m (Sec. 3.3, "Regularization").
  * ---------------------------------------------------------------------- */
 void orc_seq_weights(const uint8_t *X, int N, int L, int thr, double *w, double *meff)
 {
@@ -277,8 +277,8 @@ void orc_seq_weights(const uint8_t *X, int N, int L, int thr, double *w, double 
 }
 
 /* ------------------------------------------------------------------------
- * Weighted data frequencies, Eq. 2, followed by the pseudocount of
- * Eqs. 4-5: f_i = (1-alpha) f_i^data + alpha/q,
+ * Weighted data frequencies, Eq. 3, followed by the pseudocount of
+ * Eqs. 8-9: f_i = (1-alpha) f_i^data + alpha/q,
  *            f_ij = (1-alpha) f_ij^data + alpha/q^2  (i != j).
  * w == NULL means uniform weights (M_eff = N).  Full layout
  * fij[i][j][a][b]; reading for the unused diagonal blocks:
@@ -371,7 +371,7 @@ double orc_pearson(const double *fi, const double *fij, const int32_t *C, int M,
 }
 
 /* ------------------------------------------------------------------------
- * Boltzmann-learning step, Eq. 9 ("params update"):
+ * Boltzmann-learning step, Eq. 5 ("params update"):
  *   h_i(a)    += lr (f_i(a)    - p_i(a))
  *   J_ij(a,b) += lr (f_ij(a,b) - p_ij(a,b))   for i != j; J_ii stays 0.
  * p from the counts (layout of orc_chain_stats) divided by M; the (j,i)

@@ -31,6 +31,7 @@ SIGNATURES = {
     "bm_potts_free": (_I, [_P]),
     "bm_potts_get": (_I, [_P, _P, _P, _I, _P]),
     "bm_potts_set": (_I, [_P, _P, _P, _I, _P]),
+    "bm_device_status": (_I, [_P, _P]),
     "bm_potts_shape": (_I, [_P, _P, _P]),
     "bm_chains_init": (_I, [_P, _I, _U64, _P, _I, _P, _P]),
     "bm_chains_free": (_I, [_P]),
@@ -180,6 +181,10 @@ def bm_potts_set(m: Model, h: torch.Tensor | None = None, J: torch.Tensor | None
         raise ValueError("h and J must both be host or both be device tensors")
     where = wh if h is not None else wJ
     _check(lib().bm_potts_set(m.handle, ph, pJ, where, _stream(stream)), "bm_potts_set")
+
+
+def bm_device_status(m: Model, stream=None):
+    _check(lib().bm_device_status(m.handle, _stream(stream)), "bm_device_status")
 
 
 def bm_model_set_engine(m: Model, engine: int):

@@ -29,6 +29,7 @@ void free_model(bm_model_s *m)
     cudaFree(m->J);
     cudaFree(m->h_back);
     cudaFree(m->J_back);
+    cudaFree(m->Jg);
     cudaFree(m->dflags);
     cudaFree(m->dred);
     delete m;
@@ -88,7 +89,10 @@ int bm_potts_load(const float *h, const float *J, int L, int q, int where, void 
     LOAD_CK(cudaMalloc(&m->J, nJ * sizeof(float)));
     LOAD_CK(cudaMalloc(&m->h_back, nh * sizeof(float)));
     LOAD_CK(cudaMalloc(&m->J_back, nJ * sizeof(float)));
+    m->bs = bm_gather_block_stride(q);
+    LOAD_CK(cudaMalloc(&m->Jg, (size_t)L * L * m->bs * sizeof(float)));
     LOAD_CK(cudaMalloc(&m->dflags, 8 * sizeof(int)));
+    LOAD_CK(cudaMemsetAsync(m->dflags, 0, 8 * sizeof(int), st));
     m->red_cap = (size_t)bm_update_num_partials(L) * 5 + 8;
     LOAD_CK(cudaMalloc(&m->dred, m->red_cap * sizeof(double)));
     LOAD_CK(cudaMemcpyAsync(m->h, h, nh * sizeof(float), copy_kind(where, BM_DEVICE), st));
@@ -115,6 +119,11 @@ int bm_potts_load(const float *h, const float *J, int L, int q, int where, void 
     if (flags & 2) {
         free_model(m);
         return bm_fail(BM_EINVAL, "bm_potts_load: J[i][i] must be zero");
+    }
+    rc = bm_launch_build_gather(m->J, m->Jg, L, q, st);
+    if (rc != BM_OK) {
+        free_model(m);
+        return rc;
     }
     *out = m;
     return BM_OK;
@@ -144,7 +153,24 @@ int bm_potts_set(bm_model m, const float *h, const float *J, int where, void *st
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nh = (size_t)m->L * m->q, nJ = (size_t)m->L * m->L * m->q * m->q;
     if (h) BM_CK(cudaMemcpyAsync(m->h, h, nh * sizeof(float), copy_kind(where, BM_DEVICE), st));
-    if (J) BM_CK(cudaMemcpyAsync(m->J, J, nJ * sizeof(float), copy_kind(where, BM_DEVICE), st));
+    if (J) {
+        BM_CK(cudaMemcpyAsync(m->J, J, nJ * sizeof(float), copy_kind(where, BM_DEVICE), st));
+        return bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
+    }
+    return BM_OK;
+}
+
+int bm_device_status(bm_model m, void *stream)
+{
+    if (!m) return bm_fail(BM_EINVAL, "bm_device_status: NULL model");
+    cudaStream_t st = (cudaStream_t)stream;
+    int word = 0;
+    BM_CK(cudaMemcpyAsync(&word, m->dflags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BM_CK(cudaStreamSynchronize(st));
+    if (word) {
+        BM_CK(cudaMemsetAsync(m->dflags + 3, 0, sizeof(int), st));
+        return bm_fail(BM_ETIMEOUT, "device wait timed out in a Gibbs launch (error word 0x%x)", word);
+    }
     return BM_OK;
 }
 
@@ -359,8 +385,14 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
     bool apply = true;
     if (want) {
         double mo[5];
+        int word = 0;
         BM_CK(cudaMemcpyAsync(mo, moments, sizeof mo, cudaMemcpyDeviceToHost, st));
+        BM_CK(cudaMemcpyAsync(&word, m->dflags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
         BM_CK(cudaStreamSynchronize(st));
+        if (word) {
+            BM_CK(cudaMemsetAsync(m->dflags + 3, 0, sizeof(int), st));
+            return bm_fail(BM_ETIMEOUT, "bm_update: an earlier Gibbs launch timed out (error word 0x%x)", word);
+        }
         const double n = (double)m->L * (m->L - 1) / 2 * m->q * m->q;
         const double cov = n * mo[4] - mo[0] * mo[1];
         const double vx = n * mo[2] - mo[0] * mo[0], vy = n * mo[3] - mo[1] * mo[1];
@@ -371,6 +403,8 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
     if (apply) {
         float *t = m->h; m->h = m->h_back; m->h_back = t;
         t = m->J; m->J = m->J_back; m->J_back = t;
+        rc = bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
+        if (rc != BM_OK) return rc;
     }
     if (applied_out) *applied_out = apply ? 1 : 0;
     return BM_OK;

@@ -19,8 +19,12 @@ struct bm_model_s {
     // next iterate of bm_update (swapped in when the update is applied).
     float *h = nullptr, *J = nullptr;
     float *h_back = nullptr, *J_back = nullptr;
+    // Gather layout of the live J: Jg[i][j][b][a] = J_ij(a,b), each (i,j)
+    // block padded to bs floats (16-byte aligned blocks).
+    float *Jg = nullptr;
+    int bs = 0;
     // Small device scratch for flags / reductions (owned).
-    int *dflags = nullptr;       // [8] error / check words
+    int *dflags = nullptr;       // [8] check words; [3] = device error bits (1: wait timeout)
     double *dred = nullptr;      // reduction partials, capacity red_cap doubles
     size_t red_cap = 0;
     int num_sms = 0;
@@ -98,6 +102,8 @@ int bm_launch_check_model(const float *h, const float *J, int L, int q, int *dfl
                           cudaStream_t st);
 int bm_launch_check_symbols(const uint8_t *s, size_t n, int q, int *dflag, cudaStream_t st);
 int bm_launch_chains_init(uint8_t *s, int M, int L, int q, uint64_t seed, cudaStream_t st);
+int bm_gather_block_stride(int q);
+int bm_launch_build_gather(const float *J, float *Jg, int L, int q, cudaStream_t st);
 int bm_launch_gibbs_simt(const bm_model_s *m, bm_chains_s *c, int nsweeps, float beta,
                          cudaStream_t st);
 int bm_launch_chain_stats(const uint8_t *s, int M, int L, int q, int32_t *counts,

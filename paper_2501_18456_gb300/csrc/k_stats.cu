@@ -2,8 +2,8 @@
 // data frequencies.
 //
 //   chain counts   (Sec. 2.1, p_i and p_ij as chain frequencies)
-//   weights        (Eq. 3, identity >= threshold, w = 1/N_m; M_eff Sec. 3.4)
-//   data stats     (Eq. 2 with the pseudocount of Eqs. 4-5)
+//   weights        (Eq. 7, identity >= threshold, w = 1/N_m; M_eff Sec. 3.3)
+//   data stats     (Eq. 3 with the pseudocount of Eqs. 8-9)
 //
 // All three are histogram / counting problems over a few MB of uint8
 // states, so they run on CUDA cores with shared-memory histograms; every
@@ -168,7 +168,7 @@ __global__ void k_weight_sum(const float *__restrict__ w, int N, double *out3)
 }
 
 // ----------------------------------------------------------------------------
-// Sequence identity counts for the weights (Eq. 3).  Rows are compared four
+// Sequence identity counts for the weights (Eq. 7).  Rows are compared four
 // symbols per 32-bit word: x = a ^ b has a zero byte exactly where the
 // symbols agree; ((x & 0x7f7f7f7f) + 0x7f7f7f7f) | x has bit 7 clear exactly
 // in those bytes, so ~that & 0x80808080 marks the matches.  Per-byte match

@@ -1,4 +1,4 @@
-// Boltzmann-learning step (Eq. 9) fused with the Pearson convergence
+// Boltzmann-learning step (Eq. 5) fused with the Pearson convergence
 // check (Sec. 2.1, "Convergence criterium").
 //
 // One warp per site pair i < j walks the q*q entries of the pair block:

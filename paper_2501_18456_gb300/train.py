@@ -3,11 +3,11 @@
 Every step runs in libbmdca.so kernels; this module only sequences the C
 entry points:
 
-  preprocessing (once):  bm_seq_weights (Eq. 3) -> bm_data_stats (Eqs. 2, 4-5)
+  preprocessing (once):  bm_seq_weights (Eq. 7) -> bm_data_stats (Eqs. 3, 8-9)
   per iteration t:       bm_gibbs_sweep x nsweeps (PCD chains, theta_t)
                          -> bm_chain_stats -> bm_update: Pearson of the
                          connected correlations of theta_t's chains; stop if
-                         rho >= target (theta_t kept), else Eq. 9 -> theta_{t+1}
+                         rho >= target (theta_t kept), else Eq. 5 -> theta_{t+1}
 
 Initial parameters are the caller's choice.  `profile_init` offers the
 independent-site model h_i(a) = log f_i(a), J = 0 (finite thanks to the
@@ -26,14 +26,14 @@ from . import bmdca
 
 @dataclasses.dataclass
 class TrainConfig:
-    M: int = 10000          # persistent chains (paper default, Sec. 3.4)
-    nsweeps: int = 10       # sweeps per update (Sec. 3.4)
+    M: int = 10000          # persistent chains (paper default, Sec. 3.3)
+    nsweeps: int = 10       # sweeps per update (Sec. 3.3)
     lr: float = 0.01        # learning rate; set explicitly by every workload
     max_iters: int = 500
     target: float = 0.95    # Pearson target (Sec. 2.1)
     seed: int = 0
-    seqid: float = 0.8      # identity threshold of Eq. 3
-    pseudocount: float = -1.0  # < 0: 1 / M_eff (Sec. 3.4)
+    seqid: float = 0.8      # identity threshold of Eq. 7
+    pseudocount: float = -1.0  # < 0: 1 / M_eff (Sec. 3.3)
     reweight: bool = True
 
 

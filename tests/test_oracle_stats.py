@@ -1,6 +1,6 @@
-"""Pins of the oracle's statistics: chain counts, sequence weights (Eq. 3),
-weighted frequencies with pseudocount (Eqs. 2, 4-5), the Pearson check and
-the Boltzmann update (Eq. 9).
+"""Pins of the oracle's statistics: chain counts, sequence weights (Eq. 7),
+weighted frequencies with pseudocount (Eqs. 3, 8-9), the Pearson check and
+the Boltzmann update (Eq. 5).
 
 References: numpy one-hot einsum counts, an O(N^2 L) numpy identity matrix,
 np.corrcoef, sum rules and closed-form special cases.
@@ -187,7 +187,7 @@ def test_update_closed_form_and_symmetry(orc):
 
 
 def test_update_fixed_point(orc):
-    """f = p leaves the parameters unchanged (Eq. 9 at convergence)."""
+    """f = p leaves the parameters unchanged (Eq. 5 at convergence)."""
     M, L, q = 64, 5, 3
     S = synth.random_states(M, L, q, 16)
     fi, fij = orc.data_stats(S, None, q, 0.0)
