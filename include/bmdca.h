@@ -179,6 +179,30 @@ int bm_chain_stats(bm_chains c, int32_t *counts_dev, void *stream);
 int bm_seq_weights(const uint8_t *msa_dev, int N, int L, double seqid, float *w_dev,
                    double *meff_host, void *stream);
 
+/* Largest N accepted by bm_seq_weights_static (4 MiB of device memory). */
+#define BM_SEQ_WEIGHTS_STATIC_MAX_N 1048576
+
+/*
+ * bm_seq_weights_static -- the same weights and M_eff as bm_seq_weights,
+ * computed without allocating any device memory.  The paper has no
+ * counterpart: this is a deployment variant for callers that must not
+ * allocate, e.g. code running while another framework's caching allocator
+ * holds the device memory, serving loops that must not enter the driver's
+ * allocator (cudaMalloc/cudaFree may synchronise the device), or embedders
+ * that give the library a fixed memory budget.
+ *   Scratch: one file-scope device array of 256 B + 4 * MAX_N bytes, held
+ *   on every GPU that loads the library until the process exits.
+ *   N > BM_SEQ_WEIGHTS_STATIC_MAX_N -> BM_EINVAL (message names the limit).
+ *   The first call on a device (with that device current) looks up the
+ *   array's device address; make that first call before any stream capture.
+ *   Every call reuses the same array (its counters are cleared at the start
+ *   of each call), so calls whose GPU work overlaps -- different streams or
+ *   host threads -- race and must be serialised by the caller.
+ * Arguments, results and synchronisation are those of bm_seq_weights.
+ */
+int bm_seq_weights_static(const uint8_t *msa_dev, int N, int L, double seqid, float *w_dev,
+                          double *meff_host, void *stream);
+
 /*
  * bm_data_stats -- empirical frequencies, Eq. 3, with the pseudocount of
  * Eqs. 8-9:  f_i = (1-alpha) f_i^data + alpha/q,

@@ -44,6 +44,7 @@ SIGNATURES = {
     "bm_model_set_engine": (_I, [_P, _I]),
     "bm_chain_stats": (_I, [_P, _P, _P]),
     "bm_seq_weights": (_I, [_P, _I, _I, _D, _P, _P, _P]),
+    "bm_seq_weights_static": (_I, [_P, _I, _I, _D, _P, _P, _P]),
     "bm_data_stats": (_I, [_P, _P, _I, _I, _I, _D, _P, _P, _P]),
     "bm_update": (_I, [_P, _P, _P, _P, _I, _F, _D, _P, _P, _P]),
     "bm_energy_score": (_I, [_P, _P, _I, _P, _P]),
@@ -241,6 +242,19 @@ def bm_seq_weights(msa: torch.Tensor, w: torch.Tensor, seqid: float = 0.8, want_
     meff = ctypes.c_double()
     _check(lib().bm_seq_weights(pm, N, L, seqid, pw, ctypes.byref(meff) if want_meff else None,
                                 _stream(stream)), "bm_seq_weights")
+    return float(meff.value) if want_meff else None
+
+
+def bm_seq_weights_static(msa: torch.Tensor, w: torch.Tensor, seqid: float = 0.8,
+                          want_meff: bool = True, stream=None):
+    """bm_seq_weights without device allocation (fixed static scratch; see bmdca.h)."""
+    N, L = msa.shape
+    pm = _dev(msa, torch.uint8, N * L, "msa")
+    pw = _dev(w, torch.float32, N, "w")
+    meff = ctypes.c_double()
+    _check(lib().bm_seq_weights_static(pm, N, L, seqid, pw,
+                                       ctypes.byref(meff) if want_meff else None, _stream(stream)),
+           "bm_seq_weights_static")
     return float(meff.value) if want_meff else None
 
 
