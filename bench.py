@@ -40,12 +40,15 @@ L_SITES, Q, M_CHAINS, N_SEQS, NSWEEPS, LR, SEED = 256, 21, 10000, 50000, 10, 0.0
 WORKLOAD = "bmDCA dense protein-like: L=256 q=21 M=10000 chains, 10 sweeps/iter, MSA N=50000"
 METRIC = "Gibbs site-updates/s (L=256,q=21,M=10k)"
 UNIT = "site-updates/s"
+# DRAM bytes per launch of k_gibbs_mma from an ncu capture of this bench's
+# launch (see profiles/); None until captured for the current kernel.
+TRAFFIC_GIBBS_MMA = 1162890496 + 4183808  # read + write, 10-sweep launch (profiles/k_gibbs_mma_*)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -223,38 +226,47 @@ def run_ours(args, rank, world, local):
         rho, applied = bmdca.bm_update(model, fi, fij, counts, M_CHAINS, LR, 2.0, True)
         return rho
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
+    def measure(engine, steps, sample_clocks=False):
+        """W warm-up steps, then `steps` timed steps (L2 flushed before each)."""
+        bmdca.bm_model_set_engine(model, engine)
+        gibbs_ms.clear()
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local) if sample_clocks else None
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        t_wall0 = time.perf_counter()
+        step_events = []
+        rho = None
+        for _ in range(steps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record(st)
+            rho = step(record=True)
+            b.record(st)
+            step_events.append((a, b))
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        barrier()
+        clk = clocks.stop() if clocks else None
+        ms_s = float(np.mean([a.elapsed_time(b) for a, b in step_events]))
+        ms_g = float(np.mean([a.elapsed_time(b) for a, b in gibbs_ms]))
+        if world > 1:
+            t = torch.tensor([ms_s, ms_g], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_s, ms_g = float(t[0]), float(t[1])
+        bmdca.bm_device_status(model)
+        return ms_s, ms_g, rho, clk, t_wall
 
-    clocks = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    t_wall0 = time.perf_counter()
-    step_events = []
-    rho = None
-    for _ in range(args.steps):
-        flush.zero_()
-        a, b = ev(), ev()
-        a.record(st)
-        rho = step(record=True)
-        b.record(st)
-        step_events.append((a, b))
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall0
-    barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in step_events]
-    gib_ms = [a.elapsed_time(b) for a, b in gibbs_ms]
-    ms_step = float(np.mean(step_ms))
-    ms_gibbs = float(np.mean(gib_ms))
-    if world > 1:
-        t = torch.tensor([ms_step, ms_gibbs], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_gibbs = float(t[0]), float(t[1])
     site_updates_per_step = M_CHAINS * L_SITES * NSWEEPS
+    # plain FP32 path (CUDA-core gather) on the same workload, for comparison
+    ms_plain, ms_plain_gibbs, _, _, _ = measure(bmdca.BM_ENGINE_SIMT, max(2, args.steps // 2))
+    # headline: the library's default engine (tensor cores)
+    ms_step, ms_gibbs, rho, clk, t_wall = measure(bmdca.BM_ENGINE_AUTO, args.steps, sample_clocks=True)
     value = world * site_updates_per_step / (ms_step * 1e-3)
 
     # ---- per-row timings of the other steps (one step's worth each)
@@ -297,22 +309,25 @@ def run_ours(args, rank, world, local):
     h2d = h_pin.numel() * 4 + J_pin.numel() * 4 + s_pin.numel()
     d2h = s_out.numel() + 8
 
-    # ---- roofline of the dominant kernel (Gibbs sweep, CUDA-core FP32 gather form)
-    peaks = {}
+    # ---- roofline of the dominant kernel: the tensor-core Gibbs sweep.
+    # Algorithmic work per launch: the one-hot x J contraction of every site
+    # block, 2*M*(Lq)^2 flops per sweep, done twice (fp16 hi and lo parts of J).
+    peaks, peak_src = {}, "fallback 1700 TFLOP/s bf16 sustained"
     try:
         peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+        peak_src = "measured bf16_tflops_sustained (MEASURED_PEAKS.json)"
     except (OSError, ValueError):
         pass
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fadd_peak_tflops = sm_count * 128 * sm_max_mhz * 1e6 / 1e12  # FP32 lanes x clock, adds
-    adds_per_launch = float(M_CHAINS) * L_SITES * NSWEEPS * L_SITES * Q
-    achieved = adds_per_launch / (ms_gibbs * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fadd_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / fadd_peak_tflops, "traffic": None,
-                "kernel": "k_gibbs_simt",
-                "note": "algorithmic FP32 adds (M*L*sweeps*L*q) per launch / launch time vs FP32 "
-                        "add peak = SMs x 128 lanes x max SM clock (derived, not measured)"}
+    peak_tf = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    Qd = float(L_SITES * Q)
+    flops_per_launch = 2.0 * 2.0 * M_CHAINS * Qd * Qd * NSWEEPS
+    achieved = flops_per_launch / (ms_gibbs * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved / peak_tf, "traffic": TRAFFIC_GIBBS_MMA,
+                "kernel": "k_gibbs_mma",
+                "note": "achieved = 2 passes (fp16 hi, lo) x 2*M*(L*q)^2 flops per sweep x sweeps per "
+                        "launch / CUDA-event launch time; peak: " + peak_src +
+                        "; fp16 and bf16 share the dense rate"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -322,7 +337,10 @@ def run_ours(args, rank, world, local):
                "sample": f"oracle Gibbs sweep on {n} of the {M_CHAINS} chains, 1 sweep, "
                          f"{dt:.1f} s, FP64 C, 1 thread"}
 
-    launches_per_step = 1 + 1 + 3  # gibbs, chain_stats, update (pairs, fields, partial sum)
+    # Kernels launched per step: J tensor-core layout rebuild (the previous
+    # update changed J) + Gibbs sweep, chain counts, update (pairs, fields,
+    # Pearson partial sum) + gather-layout rebuild.
+    launches_per_step = 2 + 1 + 3 + 1
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -330,8 +348,13 @@ def run_ours(args, rank, world, local):
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "L": L_SITES, "q": Q, "M": M_CHAINS,
                            "N": N_SEQS, "nsweeps": NSWEEPS, "lr": LR, "meff": meff_box.get("m"),
-                           "engine": "simt", "l2": "flushed between steps (256 MB write)",
+                           "engine": "tensor cores (tcgen05, fp16 hi+lo J, f32 accumulate)",
+                           "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world}", "pearson_last": rho},
+                "plain_fp32": {"value": world * site_updates_per_step / (ms_plain * 1e-3), "unit": UNIT,
+                               "ms_per_step": ms_plain, "gibbs_ms_per_sweep": ms_plain_gibbs / NSWEEPS,
+                               "engine": "CUDA-core FP32 gather (k_gibbs_staged)",
+                               "speedup_of_value": ms_plain / ms_step},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": world * site_updates_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

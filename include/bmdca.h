@@ -66,8 +66,9 @@ enum { BM_HOST = 0, BM_DEVICE = 1 };
 
 /* Which kernel form bm_gibbs_sweep uses (bm_model_set_engine). */
 enum {
-    BM_ENGINE_SIMT = 0,  /* FP32 CUDA-core gather of J rows (default) */
-    BM_ENGINE_AUTO = 1   /* library picks the fastest form with FP32-class fields */
+    BM_ENGINE_SIMT = 0,  /* FP32 CUDA-core gather of J rows */
+    BM_ENGINE_AUTO = 1,  /* default: tensor cores when the shape fits, else CUDA cores */
+    BM_ENGINE_MMA = 2    /* tensor cores: one-hot x (fp16 hi + fp16 lo) J, FP32 accumulate */
 };
 
 /* Library version string, e.g. "bmdca-gb300 0.1". */
@@ -158,6 +159,23 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
 /* Select the kernel form used by bm_gibbs_sweep for this model
  * (BM_ENGINE_*).  BM_EINVAL for an unknown engine. */
 int bm_model_set_engine(bm_model m, int engine);
+
+/* Kernel form used by bm_chain_stats (bm_chains_set_stats_engine). */
+enum {
+    BM_STATS_AUTO = 0,      /* default: the fastest measured form (currently BM_STATS_SIMT) */
+    BM_STATS_SIMT = 1,      /* CUDA cores, shared-memory histograms */
+    BM_STATS_MMA_BF16 = 2,  /* tensor cores, BF16 one-hot operands */
+    BM_STATS_MMA_FP8 = 3    /* tensor cores, FP8 E4M3 one-hot operands */
+};
+
+/* Select the bm_chain_stats kernel form for these chains (all forms give
+ * identical, exact counts).  BM_EINVAL for an unknown engine. */
+int bm_chains_set_stats_engine(bm_chains c, int engine);
+
+/* Synchronise `stream` and report device-side errors recorded by earlier
+ * kernels on these chains (bounded waits that gave up): BM_OK or
+ * BM_ETIMEOUT (the error word is then cleared). */
+int bm_chains_device_status(bm_chains c, void *stream);
 
 /*
  * bm_chain_stats -- model statistics from the chains (Sec. 2.1: p_i, p_ij

@@ -20,7 +20,8 @@ _lib = None
 BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ENUMERIC, BM_ETIMEOUT, BM_EDEVICE, BM_EBUSY = (
     0, -1, -2, -3, -4, -5, -6, -7)
 BM_HOST, BM_DEVICE = 0, 1
-BM_ENGINE_SIMT, BM_ENGINE_AUTO = 0, 1
+BM_ENGINE_SIMT, BM_ENGINE_AUTO, BM_ENGINE_MMA = 0, 1, 2
+BM_STATS_AUTO, BM_STATS_SIMT, BM_STATS_MMA_BF16, BM_STATS_MMA_FP8 = 0, 1, 2, 3
 
 # name -> (restype, argtypes); kept in the order of include/bmdca.h
 _P, _I, _U64, _F, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_float, ctypes.c_double
@@ -42,6 +43,8 @@ SIGNATURES = {
     "bm_chains_shape": (_I, [_P, _P, _P]),
     "bm_gibbs_sweep": (_I, [_P, _P, _I, _F, _P]),
     "bm_model_set_engine": (_I, [_P, _I]),
+    "bm_chains_set_stats_engine": (_I, [_P, _I]),
+    "bm_chains_device_status": (_I, [_P, _P]),
     "bm_chain_stats": (_I, [_P, _P, _P]),
     "bm_seq_weights": (_I, [_P, _I, _I, _D, _P, _P, _P]),
     "bm_seq_weights_static": (_I, [_P, _I, _I, _D, _P, _P, _P]),
@@ -227,6 +230,14 @@ def bm_chains_set_sweep_counter(c: Chains, sweep: int):
 
 def bm_gibbs_sweep(m: Model, c: Chains, nsweeps: int, beta: float = 1.0, stream=None):
     _check(lib().bm_gibbs_sweep(m.handle, c.handle, nsweeps, beta, _stream(stream)), "bm_gibbs_sweep")
+
+
+def bm_chains_set_stats_engine(c: Chains, engine: int):
+    _check(lib().bm_chains_set_stats_engine(c.handle, engine), "bm_chains_set_stats_engine")
+
+
+def bm_chains_device_status(c: Chains, stream=None):
+    _check(lib().bm_chains_device_status(c.handle, _stream(stream)), "bm_chains_device_status")
 
 
 def bm_chain_stats(c: Chains, counts: torch.Tensor, stream=None):

@@ -30,6 +30,7 @@ void free_model(bm_model_s *m)
     cudaFree(m->h_back);
     cudaFree(m->J_back);
     cudaFree(m->Jg);
+    cudaFree(m->Jt);
     cudaFree(m->dflags);
     cudaFree(m->dred);
     delete m;
@@ -155,6 +156,7 @@ int bm_potts_set(bm_model m, const float *h, const float *J, int where, void *st
     if (h) BM_CK(cudaMemcpyAsync(m->h, h, nh * sizeof(float), copy_kind(where, BM_DEVICE), st));
     if (J) {
         BM_CK(cudaMemcpyAsync(m->J, J, nJ * sizeof(float), copy_kind(where, BM_DEVICE), st));
+        m->mma_current = false;
         return bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
     }
     return BM_OK;
@@ -185,7 +187,7 @@ int bm_potts_shape(bm_model m, int *L, int *q)
 int bm_model_set_engine(bm_model m, int engine)
 {
     if (!m) return bm_fail(BM_EINVAL, "bm_model_set_engine: NULL model");
-    if (engine != BM_ENGINE_SIMT && engine != BM_ENGINE_AUTO)
+    if (engine != BM_ENGINE_SIMT && engine != BM_ENGINE_AUTO && engine != BM_ENGINE_MMA)
         return bm_fail(BM_EINVAL, "bm_model_set_engine: unknown engine %d", engine);
     m->engine = engine;
     return BM_OK;
@@ -210,7 +212,11 @@ int bm_chains_init(bm_model m, int M, uint64_t seed, const uint8_t *init_or_null
     c->sweep = 0;
     const size_t n = (size_t)M * m->L;
     cudaError_t e = cudaMalloc(&c->s, n);
+    if (e == cudaSuccess) e = cudaMalloc(&c->derr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->derr, 0, sizeof(int), st);
     if (e != cudaSuccess) {
+        cudaFree(c->s);
+        cudaFree(c->derr);
         delete c;
         return bm_cuda_fail(e, "cudaMalloc(chains)");
     }
@@ -231,6 +237,7 @@ int bm_chains_init(bm_model m, int M, uint64_t seed, const uint8_t *init_or_null
     }
     if (rc != BM_OK) {
         cudaFree(c->s);
+        cudaFree(c->derr);
         delete c;
         return rc;
     }
@@ -242,7 +249,31 @@ int bm_chains_free(bm_chains c)
 {
     if (!c) return BM_OK;
     cudaFree(c->s);
+    cudaFree(c->derr);
     delete c;
+    return BM_OK;
+}
+
+int bm_chains_device_status(bm_chains c, void *stream)
+{
+    if (!c) return bm_fail(BM_EINVAL, "bm_chains_device_status: NULL chains");
+    cudaStream_t st = (cudaStream_t)stream;
+    int word = 0;
+    BM_CK(cudaMemcpyAsync(&word, c->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BM_CK(cudaStreamSynchronize(st));
+    if (word) {
+        BM_CK(cudaMemsetAsync(c->derr, 0, sizeof(int), st));
+        return bm_fail(BM_ETIMEOUT, "device wait timed out in a chain-statistics launch (error word 0x%x)", word);
+    }
+    return BM_OK;
+}
+
+int bm_chains_set_stats_engine(bm_chains c, int engine)
+{
+    if (!c) return bm_fail(BM_EINVAL, "bm_chains_set_stats_engine: NULL chains");
+    if (engine < BM_STATS_AUTO || engine > BM_STATS_MMA_FP8)
+        return bm_fail(BM_EINVAL, "bm_chains_set_stats_engine: unknown engine %d", engine);
+    c->stats_engine = engine;
     return BM_OK;
 }
 
@@ -297,7 +328,9 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
     cudaStream_t st = (cudaStream_t)stream;
     for (int done = 0; done < nsweeps;) {
         const int k = nsweeps - done < kMaxSweepsPerLaunch ? nsweeps - done : kMaxSweepsPerLaunch;
-        const int rc = bm_launch_gibbs_simt(m, c, k, beta, st);
+        const bool mma = m->engine == BM_ENGINE_MMA ||
+                         (m->engine == BM_ENGINE_AUTO && bm_gibbs_mma_chains_per_cta(m, c->M) > 0);
+        const int rc = mma ? bm_launch_gibbs_mma(m, c, k, beta, st) : bm_launch_gibbs_simt(m, c, k, beta, st);
         if (rc != BM_OK) return rc;
         c->sweep += (uint64_t)k;
         done += k;
@@ -308,7 +341,19 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
 int bm_chain_stats(bm_chains c, int32_t *counts_dev, void *stream)
 {
     if (!c || !counts_dev) return bm_fail(BM_EINVAL, "bm_chain_stats: NULL argument");
-    return bm_launch_chain_stats(c->s, c->M, c->L, c->q, counts_dev, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool mma_ok = c->M < (1 << 24);  // FP32 accumulation is exact below 2^24
+    switch (c->stats_engine) {
+    case BM_STATS_MMA_BF16:
+        if (mma_ok) return bm_launch_chain_stats_mma(c->s, c->M, c->L, c->q, counts_dev, 2, c->derr, st);
+        break;
+    case BM_STATS_MMA_FP8:
+        if (mma_ok) return bm_launch_chain_stats_mma(c->s, c->M, c->L, c->q, counts_dev, 1, c->derr, st);
+        break;
+    default:  // BM_STATS_AUTO, BM_STATS_SIMT: the shared-memory histogram form is the faster one
+        break;
+    }
+    return bm_launch_chain_stats(c->s, c->M, c->L, c->q, counts_dev, st);
 }
 
 int bm_seq_weights(const uint8_t *msa_dev, int N, int L, double seqid, float *w_dev,
@@ -403,6 +448,7 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
     if (apply) {
         float *t = m->h; m->h = m->h_back; m->h_back = t;
         t = m->J; m->J = m->J_back; m->J_back = t;
+        m->mma_current = false;
         rc = bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
         if (rc != BM_OK) return rc;
     }

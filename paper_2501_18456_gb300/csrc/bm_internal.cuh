@@ -14,7 +14,7 @@
 struct bm_model_s {
     int L = 0, q = 0;
     int device = 0;
-    int engine = BM_ENGINE_SIMT;
+    int engine = BM_ENGINE_AUTO;
     // Parameters: front buffer is the live model, back buffer receives the
     // next iterate of bm_update (swapped in when the update is applied).
     float *h = nullptr, *J = nullptr;
@@ -23,6 +23,14 @@ struct bm_model_s {
     // block padded to bs floats (16-byte aligned blocks).
     float *Jg = nullptr;
     int bs = 0;
+    // Tensor-core layout of the live J: fp16 hi/lo parts, rows (i,a), Kp
+    // columns (j,b) (zero padded to a multiple of 64) in 64-column slabs
+    // with hi and lo interleaved, and its TMA tensor map (CUtensorMap, 128
+    // bytes).  Rebuilt lazily when stale.
+    void *Jt = nullptr;
+    int Kp = 0;
+    bool mma_current = false;
+    alignas(64) unsigned char tmap_j[128] = {};
     // Small device scratch for flags / reductions (owned).
     int *dflags = nullptr;       // [8] check words; [3] = device error bits (1: wait timeout)
     double *dred = nullptr;      // reduction partials, capacity red_cap doubles
@@ -36,6 +44,8 @@ struct bm_chains_s {
     uint8_t *s = nullptr;  // [M][L]
     uint64_t seed = 0;
     uint64_t sweep = 0;    // Philox sweep word of the next sweep
+    int stats_engine = BM_STATS_AUTO;
+    int *derr = nullptr;   // device error word of this handle's kernels
 };
 
 // ---------------------------------------------------------------------------
@@ -102,12 +112,16 @@ int bm_launch_check_model(const float *h, const float *J, int L, int q, int *dfl
                           cudaStream_t st);
 int bm_launch_check_symbols(const uint8_t *s, size_t n, int q, int *dflag, cudaStream_t st);
 int bm_launch_chains_init(uint8_t *s, int M, int L, int q, uint64_t seed, cudaStream_t st);
+int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M);
+int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
 int bm_gather_block_stride(int q);
 int bm_launch_build_gather(const float *J, float *Jg, int L, int q, cudaStream_t st);
 int bm_launch_gibbs_simt(const bm_model_s *m, bm_chains_s *c, int nsweeps, float beta,
                          cudaStream_t st);
 int bm_launch_chain_stats(const uint8_t *s, int M, int L, int q, int32_t *counts,
                           cudaStream_t st);
+int bm_launch_chain_stats_mma(const uint8_t *s, int M, int L, int q, int32_t *counts, int elem_bytes,
+                              int *err, cudaStream_t st);
 int bm_launch_seq_weights(const uint8_t *msa, int N, int L, int thr, float *w, int *cnt,
                           double *meff_dev, cudaStream_t st);
 int bm_launch_data_stats(const uint8_t *msa, const float *w, int N, int L, int q, double alpha,

@@ -29,8 +29,14 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def load(bm, h, J):
-    return bm.bm_potts_load(to_dev(h), to_dev(J))
+GIBBS_ENGINES = ["simt", "mma"]
+
+
+def load(bm, h, J, engine=None):
+    m = bm.bm_potts_load(to_dev(h), to_dev(J))
+    if engine is not None:
+        bm.bm_model_set_engine(m, {"simt": bm.BM_ENGINE_SIMT, "mma": bm.BM_ENGINE_MMA}[engine])
+    return m
 
 
 def states_of(bm, c):
@@ -81,13 +87,16 @@ def test_chains_init_from_states_and_symbol_check(bm):
     (129, 24, 32, 1.2),    # largest alphabet
     (45, 9, 3, 1.0),
     (17, 2, 1, 1.0),       # degenerate alphabet
+    (200, 61, 4, 1.0),     # several blocks of 32 sites, ragged tail
 ])
-def test_gibbs_single_sweep_teacher_forced(bm, orc, M, L, q, beta):
+@pytest.mark.parametrize("engine", GIBBS_ENGINES)
+def test_gibbs_single_sweep_teacher_forced(bm, orc, M, L, q, beta, engine):
     h, J = synth.planted_local_model(L, q, 5, sigma_h=1.0, sigma_J=0.3)
-    m = load(bm, h, J)
+    m = load(bm, h, J, engine)
     c = bm.bm_chains_init(m, M, 99)
     s0 = states_of(bm, c)
     bm.bm_gibbs_sweep(m, c, 1, beta)
+    bm.bm_device_status(m)
     s1 = states_of(bm, c)
     check_sweep(orc, h, J, s0, s1, 99, 0, beta)
     assert bm.bm_chains_sweep_counter(c) == 1
@@ -95,24 +104,27 @@ def test_gibbs_single_sweep_teacher_forced(bm, orc, M, L, q, beta):
         assert (s1 != s0).mean() > 0.05
 
 
-def test_gibbs_consecutive_sweeps_each_verified(bm, orc):
+@pytest.mark.parametrize("engine", GIBBS_ENGINES)
+def test_gibbs_consecutive_sweeps_each_verified(bm, orc, engine):
     L, q, M = 20, 21, 300
     h, J = synth.planted_contact_model(L, q, 6, frac=0.2)
-    m = load(bm, h, J)
+    m = load(bm, h, J, engine)
     c = bm.bm_chains_init(m, M, 4)
     prev = states_of(bm, c)
     for k in range(4):
         bm.bm_gibbs_sweep(m, c, 1, 1.0)
+        bm.bm_device_status(m)
         cur = states_of(bm, c)
         check_sweep(orc, h, J, prev, cur, 4, k)
         prev = cur
 
 
-def test_gibbs_multi_sweep_call_equals_single_calls(bm):
+@pytest.mark.parametrize("engine", GIBBS_ENGINES)
+def test_gibbs_multi_sweep_call_equals_single_calls(bm, engine):
     """nsweeps in one call == the same sweeps one by one (keyed RNG)."""
     L, q, M = 33, 21, 500
     h, J = synth.planted_local_model(L, q, 7)
-    m = load(bm, h, J)
+    m = load(bm, h, J, engine)
     a = bm.bm_chains_init(m, M, 8)
     b = bm.bm_chains_init(m, M, 8)
     bm.bm_gibbs_sweep(m, a, 5, 1.0)
@@ -122,12 +134,13 @@ def test_gibbs_multi_sweep_call_equals_single_calls(bm):
     assert bm.bm_chains_sweep_counter(a) == bm.bm_chains_sweep_counter(b) == 5
 
 
-def test_gibbs_free_run_matches_oracle(bm, orc):
+@pytest.mark.parametrize("engine", GIBBS_ENGINES)
+def test_gibbs_free_run_matches_oracle(bm, orc, engine):
     """Three free-running sweeps: chains whose every draw is far from a CDF
     boundary are identical to the oracle's."""
     L, q, M = 16, 21, 256
     h, J = synth.planted_local_model(L, q, 9)
-    m = load(bm, h, J)
+    m = load(bm, h, J, engine)
     c = bm.bm_chains_init(m, M, 10)
     s0 = states_of(bm, c)
     bm.bm_gibbs_sweep(m, c, 3, 1.0)
@@ -137,18 +150,20 @@ def test_gibbs_free_run_matches_oracle(bm, orc):
     assert same > 0.99
 
 
-def test_gibbs_config2_launch_sampled_chains(bm, orc):
+@pytest.mark.parametrize("engine", GIBBS_ENGINES)
+def test_gibbs_config2_launch_sampled_chains(bm, orc, engine):
     """Full-size launch (L=256, q=21, M=10000, contact-map model): one sweep,
     a sample of chains across CTAs and the ragged tail verified by the oracle."""
     L, q, M = 256, 21, 10000
     h, J = synth.planted_contact_model(L, q, 11)
-    m = load(bm, h, J)
+    m = load(bm, h, J, engine)
     c = bm.bm_chains_init(m, M, 2024)
     s0 = states_of(bm, c)
     bm.bm_gibbs_sweep(m, c, 1, 1.0)
+    bm.bm_device_status(m)
     s1 = states_of(bm, c)
     rng = np.random.default_rng(0)
-    sample = sorted(set(rng.choice(M, 24, replace=False).tolist()) | {0, 65, 66, M - 1})
+    sample = sorted(set(rng.choice(M, 24, replace=False).tolist()) | {0, 65, 66, 79, 80, M - 1})
     h64, J64 = h.astype(np.float64), J.astype(np.float64)
     for k in sample:
         bad, worst, _ = orc.gibbs_verify(h64, J64, s0[k:k + 1], s1[k:k + 1], 2024, 0, 1.0, k)
@@ -207,27 +222,42 @@ def upper_blocks_numpy(S, q, pairs):
     return out
 
 
-@pytest.mark.parametrize("M,L,q", [(1024, 16, 21), (333, 37, 5), (1, 3, 2), (700, 70, 32), (50, 1, 4)])
-def test_chain_stats_bit_exact(bm, orc, M, L, q):
+STATS_ENGINES = ["simt", "mma_bf16", "mma_fp8"]
+
+
+def set_stats_engine(bm, c, name):
+    bm.bm_chains_set_stats_engine(c, {"simt": bm.BM_STATS_SIMT, "mma_bf16": bm.BM_STATS_MMA_BF16,
+                                      "mma_fp8": bm.BM_STATS_MMA_FP8}[name])
+
+
+@pytest.mark.parametrize("engine", STATS_ENGINES)
+@pytest.mark.parametrize("M,L,q", [(1024, 16, 21), (333, 37, 5), (1, 3, 2), (700, 70, 32), (50, 1, 4),
+                                   (129, 300, 21)])
+def test_chain_stats_bit_exact(bm, orc, M, L, q, engine):
     h, J = synth.planted_local_model(L, q, 4)
     m = load(bm, h, J)
     S = synth.random_states(M, L, q, 5)
     c = bm.bm_chains_init(m, M, 0, to_dev(S))
+    set_stats_engine(bm, c, engine)
     counts = torch.full((bm.n_blocks(L), q, q), -7, dtype=torch.int32, device=DEV)
     bm.bm_chain_stats(c, counts)
+    bm.bm_chains_device_status(c)
     torch.cuda.synchronize()
     assert np.array_equal(counts.cpu().numpy(), orc.chain_stats(S, q))
 
 
-def test_chain_stats_config2_properties_and_samples(bm, orc):
+@pytest.mark.parametrize("engine", STATS_ENGINES)
+def test_chain_stats_config2_properties_and_samples(bm, orc, engine):
     L, q, M = 256, 21, 10000
     h, J = synth.planted_contact_model(L, q, 3)
     m = load(bm, h, J)
     c = bm.bm_chains_init(m, M, 77)
+    set_stats_engine(bm, c, engine)
     bm.bm_gibbs_sweep(m, c, 2, 1.0)
     S = states_of(bm, c)
     counts = torch.full((bm.n_blocks(L), q, q), -1, dtype=torch.int32, device=DEV)
     bm.bm_chain_stats(c, counts)
+    bm.bm_chains_device_status(c)
     C = counts.cpu().numpy().astype(np.int64)
     assert C.min() >= 0
     diag = np.array([orc.block_index(L, i, i) for i in range(L)])
