@@ -31,12 +31,14 @@
 //   warp 1     allocates TMEM, one thread issues tcgen05.mma (M = 128 rows
 //              (i,a), N = NC chains, K = 16 per instruction, hi and lo) and
 //              commits each stage back to its producers;
-//   warps 2-5  workers: build the one-hot operand tile (NC rows x 64 K, no
-//              swizzle) of each K chunk from the chain states in shared
-//              memory; after the last chunk of a block read the accumulator
+//   warps 2-5  drawers: after the last chunk of a block read the accumulator
 //              (tcgen05.ld, one TMEM lane = one row (i,a) per thread) into
 //              shared memory, then redraw the block's sites, one thread per
-//              chain.
+//              chain, with the in-block corrections from coupling blocks
+//              staged by bulk copies;
+//   warps 6-9  generators: build the one-hot operand tile (NC rows x 64 K,
+//              no swizzle) of each K chunk from the chain states in shared
+//              memory, one thread per chain.
 // Every mbarrier wait is bounded by %globaltimer (2 s); a timeout sets an
 // abort flag and bit 2 of the model's device error word, every role leaves
 // its loop, the producer waits (bounded) for its own copies, TMEM is
@@ -347,13 +349,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
             long long t = 0;
+            int s = 0, lap = 0;  // t = lap * kNS + s
             bool ok = true;
             for (long long kb = 0; kb < nblocks && ok; ++kb) {
                 const BlockGeo g = block_geo(p, kb);
                 for (int c = 0; c < p.nK + g.nD; ++c, ++t) {
-                    const int s = (int)(t % kNS);
-                    const long long n = t / kNS;
-                    if (n > 0 && !mbar_wait(empty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag, p.err)) {
+                    if (lap > 0 && !mbar_wait(empty + 8 * s, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
                         ok = false;
                         break;
                     }
@@ -361,6 +362,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                     mbar_expect_tx(full_a + 8 * s, 2 * kTileA);
                     // one op: slabs (hi, lo) of K chunk x/64 for 128 rows
                     tma_load_3d(su32(base + lay.a + s * 2 * kTileA), &tm_j, 0, g.i0 * q, 2 * (x / kKC), full_a + 8 * s);
+                    if (++s == kNS) {
+                        s = 0;
+                        ++lap;
+                    }
                 }
             }
             if (*abort_flag) {
@@ -374,7 +379,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
         if (lane == 0) {
             // kind::f16: D F32 (bit 4), A = B = F16 (0), K-major, N >> 3 at 17, M >> 4 at 24.
             const uint32_t idesc = (1u << 4) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kRowsA >> 4) << 24);
-            long long t = 0;
+            int s = 0;
+            uint32_t ph = 0;  // stage and phase parity of the current chunk
             bool ok = true;
             for (long long kb = 0; kb < nblocks && ok; ++kb) {
                 const BlockGeo g = block_geo(p, kb);
@@ -385,9 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dcol = tmem + (uint32_t)buf * p.acc_stride;
-                for (int c = 0; c < p.nK + g.nD; ++c, ++t) {
-                    const int s = (int)(t % kNS);
-                    const uint32_t ph = (uint32_t)((t / kNS) & 1);
+                for (int c = 0; c < p.nK + g.nD; ++c) {
                     if (!mbar_wait(full_a + 8 * s, ph, abort_flag, p.err) ||
                         !mbar_wait(full_b + 8 * s, ph, abort_flag, p.err)) {
                         ok = false;
@@ -403,6 +407,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                         mma_f16(dcol, desc_sw128(al + kk * 32), bd, idesc, 1u);
                     }
                     mma_commit(empty + 8 * s);
+                    if (++s == kNS) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 mma_commit(acc_full + 8 * buf);
@@ -509,8 +517,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
         }
     } else {
         // ------------------------------------------------------------ generators (warps 6-9)
+        // Thread w owns the operand row of chain w (NC <= 128): per K chunk it
+        // zeroes the row (8 x 16-byte stores) and then stores the few nonzero
+        // halfwords (same thread, so program order keeps the stores ordered).
+        // A main chunk holds +1 at (j, s_j) for the sites j it overlaps; a
+        // delta chunk holds +1 at (j, new s_j) and -1 at (j, old s_j) for the
+        // changed sites of the previous block.
         const int w = tid - 192;  // 0..127
-        long long t = 0;
+        const bool own = w < NC;
+        unsigned char *const row0 = base + lay.b + noswz_off(own ? w : 0, 0);
+        const uint8_t *const strow = st + (own ? w : 0) * Sst;
+        int s = 0, lap = 0;  // stage and ring lap of the current chunk
         bool ok = true;
         for (long long kb = 0; kb < nblocks && ok; ++kb) {
             const BlockGeo g = block_geo(p, kb);
@@ -520,34 +537,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                 ok = false;
                 break;
             }
-            const uint8_t *psnap = snap + (buf ^ 1) * NC * kSnapStride;  // block kb-1 before its redraw
-            for (int c = 0; c < p.nK + g.nD; ++c, ++t) {
+            const uint8_t *psrow = snap + (buf ^ 1) * NC * kSnapStride + (own ? w : 0) * kSnapStride;
+            const int pi0 = kb > 0 ? g.pi0 : L, pi1 = kb > 0 ? g.pi0 + g.pBk : L;  // block kb-1's sites
+            for (int c = 0; c < p.nK + g.nD; ++c) {
                 const bool delta = c >= p.nK;
                 if (c == p.nK &&
                     !mbar_wait(ready + 8 * (buf ^ 1), (uint32_t)(((kb - 1) >> 1) & 1), abort_flag, p.err)) {
                     ok = false;
                     break;
                 }
-                const int s = (int)(t % kNS);
-                const long long n = t / kNS;
-                if (n > 0 && !mbar_wait(empty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag, p.err)) {
+                if (lap > 0 && !mbar_wait(empty + 8 * s, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
                     ok = false;
                     break;
                 }
                 const int k0 = (delta ? g.d0 + (c - p.nK) : c) * kKC;
-                unsigned char *bt = base + lay.b + s * NC * 128;
-                const int jlo = delta ? 0 : jtab[2 * c], jhi = delta ? -1 : jtab[2 * c + 1];
-                for (int ch = w; ch < NC; ch += 128) {
-                    // zero the row, then store the few nonzero halfwords (same
-                    // thread, so program order keeps the stores ordered)
-                    unsigned char *rowp = bt + noswz_off(ch, 0);
+                unsigned char *rowp = row0 + s * NC * 128;
+                if (own) {
 #pragma unroll
                     for (int pc = 0; pc < 8; ++pc)
                         *reinterpret_cast<uint4 *>(rowp + pc * 128) = make_uint4(0, 0, 0, 0);
                     if (!delta) {
+                        const int jlo = jtab[2 * c], jhi = jtab[2 * c + 1];
                         for (int j = jlo; j <= jhi; ++j) {
-                            const bool prev = (kb > 0) && j >= g.pi0 && j < g.pi0 + g.pBk;
-                            const int sj = prev ? psnap[ch * kSnapStride + (j - g.pi0)] : st[ch * Sst + j];
+                            const int sj = (j >= pi0 && j < pi1) ? psrow[j - pi0] : strow[j];
                             const int pos = j * q + sj - k0;
                             if (pos >= 0 && pos < kKC)
                                 *reinterpret_cast<unsigned short *>(rowp + (pos >> 3) * 128 + (pos & 7) * 2) = 0x3c00u;
@@ -555,7 +567,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                     } else {
                         for (int x = 0; x < g.pBk; ++x) {
                             const int j = g.pi0 + x;
-                            const int sn = st[ch * Sst + j], so = psnap[ch * kSnapStride + x];
+                            const int sn = strow[j], so = psrow[x];
                             if (sn == so) continue;
                             const int pn = j * q + sn - k0, po = j * q + so - k0;
                             if (pn >= 0 && pn < kKC)
@@ -568,6 +580,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(full_b + 8 * s);
+                if (++s == kNS) {
+                    s = 0;
+                    ++lap;
+                }
             }
         }
         if (!ok) *abort_flag = 1;
@@ -651,14 +667,15 @@ int make_map(CUtensorMap *map, const __half *ptr, int rows, int Kp)
 
 }  // namespace
 
-// Chains per CTA for the tensor-core sweep (multiple of 16, <= 256), or 0
+// Chains per CTA for the tensor-core sweep (multiple of 16, <= 128), or 0
 // when the shape does not fit one CTA's shared memory.
 int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M)
 {
+    if (m->L > 65535) return 0;  // site indices of the chunk table are 16-bit
     const int nsm = m->num_sms > 0 ? m->num_sms : 1;
     int nc = (M + nsm - 1) / nsm;
     nc = std::max(16, (nc + 15) & ~15);
-    nc = std::min(nc, 256);
+    nc = std::min(nc, 128);  // one operand-row generator thread per chain
     const int Lp = (m->L + 15) & ~15;
     const int B = std::min(kBmax, kRowsA / m->q);
     const int nK = (m->L * m->q + kKC - 1) / kKC;

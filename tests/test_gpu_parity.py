@@ -88,6 +88,8 @@ def test_chains_init_from_states_and_symbol_check(bm):
     (45, 9, 3, 1.0),
     (17, 2, 1, 1.0),       # degenerate alphabet
     (200, 61, 4, 1.0),     # several blocks of 32 sites, ragged tail
+    (150, 40, 8, 1.0),     # operand rows with 8 or 9 nonzeros per K chunk
+    (90, 30, 9, 1.0),      # operand rows with exactly 8 nonzeros per K chunk
 ])
 @pytest.mark.parametrize("engine", GIBBS_ENGINES)
 def test_gibbs_single_sweep_teacher_forced(bm, orc, M, L, q, beta, engine):
