@@ -40,9 +40,10 @@ L_SITES, Q, M_CHAINS, N_SEQS, NSWEEPS, LR, SEED = 256, 21, 10000, 50000, 10, 0.0
 WORKLOAD = "bmDCA dense protein-like: L=256 q=21 M=10000 chains, 10 sweeps/iter, MSA N=50000"
 METRIC = "Gibbs site-updates/s (L=256,q=21,M=10k)"
 UNIT = "site-updates/s"
-# DRAM bytes per launch of k_gibbs_mma from an ncu capture of this bench's
-# launch (see profiles/); None until captured for the current kernel.
-TRAFFIC_GIBBS_MMA = 1162890496 + 4183808  # read + write, 10-sweep launch (profiles/k_gibbs_mma_*)
+# DRAM bytes per launch of k_gibbs_mma (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of this bench's 10-sweep launch);
+# set to None whenever the kernel changes until it is captured again.
+TRAFFIC_GIBBS_MMA = 1304744448 + 3926784
 
 
 def parse():
