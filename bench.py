@@ -43,7 +43,7 @@ UNIT = "site-updates/s"
 # DRAM bytes per launch of k_gibbs_mma (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of this bench's 10-sweep launch);
 # set to None whenever the kernel changes until it is captured again.
-TRAFFIC_GIBBS_MMA = 1304744448 + 3926784
+TRAFFIC_GIBBS_MMA = 1189350656 + 3484160
 
 
 def parse():

@@ -23,14 +23,17 @@ struct bm_model_s {
     // block padded to bs floats (16-byte aligned blocks).
     float *Jg = nullptr;
     int bs = 0;
-    // Tensor-core layout of the live J: fp16 hi/lo parts, rows (i,a), Kp
-    // columns (j,b) (zero padded to a multiple of 64) in 64-column slabs
-    // with hi and lo interleaved, and its TMA tensor map (CUtensorMap, 128
-    // bytes).  Rebuilt lazily when stale.
+    // Tensor-core layout of the live J: fp16 hi/lo parts, 128 rows per site
+    // block (rows (i,a) of the block, zero padded), Kp columns (j,b) (zero
+    // padded to a multiple of 64) in 64-column slabs with hi and lo
+    // interleaved, and two TMA tensor maps over it (CUtensorMap, 128 bytes
+    // each): 256-row boxes of both slabs (two consecutive blocks) and
+    // 128-row boxes of one slab.  Rebuilt lazily when stale.
     void *Jt = nullptr;
     int Kp = 0;
     bool mma_current = false;
     alignas(64) unsigned char tmap_j[128] = {};
+    alignas(64) unsigned char tmap_j1[128] = {};
     // Small device scratch for flags / reductions (owned).
     int *dflags = nullptr;       // [8] check words; [3] = device error bits (1: wait timeout)
     double *dred = nullptr;      // reduction partials, capacity red_cap doubles

@@ -7,16 +7,30 @@
 // coupling rows (i,a) with the one-hot state X[m][(j,b)] = [s_j^m == b].
 //
 // Block-sequential exact Gibbs.  The sites are processed in blocks of B =
-// floor(128/q) consecutive sites.  For a block, one MMA computes
-//     G[(i,a), m] = sum_{(j,b)} J_ij(a,b) X0[m][(j,b)]
-// for all its sites and all the CTA's chains from the states X0 at the start
-// of the block (J_ii = 0, so site i's own state does not enter).  The sites
-// of the block are then redrawn in order; for site i the sites j < i of the
-// same block that already changed are corrected exactly,
-//     H_i(a) = h_i(a) + G[(i,a), m] + sum_{j in block, j < i, s_j != s0_j}
-//              (J_ij(a, s_j) - J_ij(a, s0_j)),
+// floor(128/q) consecutive sites (global block counter kb over the launch,
+// block kb covers sites of block kb mod nb of sweep kb / nb).  The MMAs
+// compute, for the 128 rows (i,a) of a block and all the CTA's chains,
+//     G[(i,a), m] = sum_{(j,b)} J_ij(a,b) X[m][(j,b)]
+// for the states at the start of the block (J_ii = 0, so site i's own state
+// does not enter).  The block's sites are then redrawn in order; for site i
+// the sites j < i of the same block that already changed are corrected
+// exactly, H_i(a) = h_i(a) + G[(i,a), m] + sum (J_ij(a, s_j) - J_ij(a, s0_j)),
 // which is the same conditional as sequential Gibbs (only the floating-point
 // summation order differs).
+//
+// Paired blocks.  Blocks are taken in pairs P = (2P, 2P+1).  One one-hot
+// operand tile of a K chunk feeds the MMAs of both blocks of the pair, which
+// halves the operand generation per flop.  Schedule of pair P (each step a
+// run of 64-column K chunks):
+//   A  main chunks [0, X) into both accumulators, built from the states
+//      after block 2P-3 with blocks 2P-2 and 2P-1 taken from their
+//      pre-redraw snapshots (those two blocks are being redrawn meanwhile);
+//   B  delta chunks of block 2P-2 (+1 at the new, -1 at the old state of
+//      each changed site) into block 2P-1's accumulator, which completes it;
+//   C  main chunks [X, nK) into both accumulators;
+//   D  delta chunks of blocks 2P-2 and 2P-1 into both accumulators, which
+//      completes block 2P (block 2P+1 is completed by step B of pair P+1).
+// So block 2P sees the states after 2P-1 and block 2P+1 those after 2P.
 //
 // Precision.  J = J_hi + J_lo with J_hi = fp16(J) and J_lo = fp16(J - J_hi)
 // (subnormals kept), two MMAs per K step accumulate into one FP32 TMEM
@@ -24,21 +38,23 @@
 // <= 2^-22 |J| per coupling (plus 2^-25 absolute below fp16's normal
 // range), i.e. FP32-class fields.
 //
-// Data path per CTA (one CTA per SM, NC chains, NC a multiple of 16):
+// Data path per CTA (one CTA per SM, NC <= 128 chains, NC a multiple of 16):
 //   warp 0     TMA producer: J_hi / J_lo tiles of 128 rows x 64 K (128-byte
-//              rows, 128B swizzle) into a 3-stage ring, completion counted on
-//              an mbarrier;
-//   warp 1     allocates TMEM, one thread issues tcgen05.mma (M = 128 rows
-//              (i,a), N = NC chains, K = 16 per instruction, hi and lo) and
-//              commits each stage back to its producers;
-//   warps 2-5  drawers: after the last chunk of a block read the accumulator
-//              (tcgen05.ld, one TMEM lane = one row (i,a) per thread) into
-//              shared memory, then redraw the block's sites, one thread per
-//              chain, with the in-block corrections from coupling blocks
-//              staged by bulk copies;
+//              rows, 128B swizzle) of both blocks of the pair into a 2-slot
+//              ring, one 64 KB copy when the two blocks are consecutive
+//              (the layout pads every block to 128 rows);
+//   warp 1     allocates TMEM (four accumulators, block kb in slot kb % 4),
+//              one thread issues tcgen05.mma (M = 128 rows (i,a), N = NC
+//              chains, K = 16 per instruction, hi and lo) and commits each
+//              ring slot back to its producer;
+//   warps 2-5  drawers: per site, read its q accumulator rows (tcgen05.ld,
+//              one TMEM lane = one row (i,a) per thread) into shared memory,
+//              then redraw it, one thread per chain, with the
+//              in-block corrections from coupling blocks staged by bulk
+//              copies; they also take the snapshots;
 //   warps 6-9  generators: build the one-hot operand tile (NC rows x 64 K,
-//              no swizzle) of each K chunk from the chain states in shared
-//              memory, one thread per chain.
+//              no swizzle) of each K chunk into a 3-slot ring, one thread
+//              per chain.
 // Every mbarrier wait is bounded by %globaltimer (2 s); a timeout sets an
 // abort flag and bit 2 of the model's device error word, every role leaves
 // its loop, the producer waits (bounded) for its own copies, TMEM is
@@ -53,12 +69,16 @@
 
 namespace {
 
-constexpr int kNS = 3;                 // pipeline stages
+constexpr int kNA = 2;                 // coupling-tile ring slots (hi and lo of two blocks, 64 KB each)
+constexpr int kNB = 3;                 // one-hot tile ring slots (NC x 128 bytes each)
 constexpr int kKC = 64;                // fp16 K elements per chunk (128-byte rows)
 constexpr int kRowsA = 128;            // MMA M
-constexpr int kTileA = kRowsA * 128;   // bytes of one A tile (16 KB)
+constexpr int kTileA = kRowsA * 128;   // bytes of one hi or lo tile (16 KB)
+constexpr int kSlotA = 4 * kTileA;     // ring slot: [hi, lo][block 0, block 1] tiles
+constexpr int kQmax = 32;              // largest alphabet
 constexpr int kThreads = 320;          // 10 warps
 constexpr int kBmax = 32;              // max sites per block
+constexpr int kNBars = 2 * kNA + 2 * kNB + 4 + 4 + 2 + 1;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -192,15 +212,16 @@ struct MmaArgs {
     int *err;
     uint64_t seed, sweep0;
     float beta;
-    int M, L, q, Lp, bs, B, nb, nK, NC, nsweeps;
-    uint32_t tmem_cols, acc_stride;  // TMEM columns allocated; column offset of accumulator 1
+    int M, L, q, Lp, bs, B, nb, nK, X, NC, nsweeps;
+    long long nblocks;
+    uint32_t tmem_cols, acc_stride;  // TMEM columns allocated; columns per accumulator
 };
 
 // Row strides of the per-chain byte arrays, padded to an odd number of
 // 32-bit words so that threads reading the same column of different chains
 // hit different banks.
 __host__ __device__ inline int st_stride(int Lp) { return Lp + 4; }
-constexpr int kSnapStride = kBmax + 4;
+__host__ __device__ inline int snap_stride(int B) { return 4 * (((B + 3) / 4) | 1); }
 
 // Shared-memory carve-up (offsets from the 1024-aligned base).
 struct Smem {
@@ -210,57 +231,109 @@ struct Smem {
 __host__ __device__ inline Smem smem_layout(int NC, int Lp, int B, int bs, int nK)
 {
     Smem s;
-    s.a = 0;                                    // stage s: hi tile at +0, lo tile at +kTileA
-    s.b = s.a + kNS * 2 * kTileA;
-    s.hs = s.b + kNS * NC * 128;
-    s.st = s.hs + kRowsA * (NC + 1) * 4;
-    s.snap = s.st + NC * st_stride(Lp);         // 2 x [NC][kSnapStride]
-    s.corr = (s.snap + 2 * NC * kSnapStride + 15) & ~15u;
+    s.a = 0;                                      // slot: hi tiles at +0, +kTileA; lo at +2, +3 kTileA
+    s.b = s.a + kNA * kSlotA;
+    s.hs = s.b + kNB * NC * 128;
+    s.st = s.hs + kQmax * (NC + 1) * 4;           // fields of one site: [a][chain]
+    s.snap = s.st + NC * st_stride(Lp);           // [2 pair slots][2 blocks][NC][snap_stride]
+    s.corr = (s.snap + 4 * NC * snap_stride(B) + 15) & ~15u;
     s.hrow = s.corr + (uint32_t)(B * (B - 1) / 2) * bs * 4;  // staged J_ij blocks, j < i in the block
-    s.jtab = s.hrow + kRowsA * 4;                // block's h rows
-    s.bars = (s.jtab + nK * 4 + 15) & ~15u;      // first/last site of each main chunk
-    s.misc = s.bars + (3 * kNS + 7) * 8;
+    s.jtab = s.hrow + kRowsA * 4;                 // block's h rows
+    s.bars = (s.jtab + nK * 4 + 15) & ~15u;       // first/last site of each K chunk
+    s.misc = s.bars + kNBars * 8;
     s.total = s.misc + 16;
     return s;
 }
 
-// Block geometry shared by all roles: sites [i0, i0 + Bk) of block kb (global
-// block counter over the launch), and the delta chunks that carry the
-// previous block's changes: K chunks [d0, d0 + nD) covering its columns.
-struct BlockGeo {
-    int i0, Bk, pi0, pBk, d0, nD;
+// Sites [i0, i0 + Bk) of block kb.
+struct Blk {
+    int i0, Bk;
 };
 
-__device__ __forceinline__ BlockGeo block_geo(const MmaArgs &p, long long kb)
+__device__ __forceinline__ Blk blk_of(const MmaArgs &p, long long kb)
 {
-    BlockGeo g;
-    const int blk = (int)(kb % p.nb);
-    g.i0 = blk * p.B;
+    Blk g;
+    g.i0 = (int)(kb % p.nb) * p.B;
     g.Bk = min(p.B, p.L - g.i0);
-    if (kb == 0) {
-        g.pi0 = g.pBk = g.d0 = g.nD = 0;
-    } else {
-        const int pb = (int)((kb - 1) % p.nb);
-        g.pi0 = pb * p.B;
-        g.pBk = min(p.B, p.L - g.pi0);
-        const int c_lo = g.pi0 * p.q, c_hi = (g.pi0 + g.pBk) * p.q;
-        g.d0 = c_lo / kKC;
-        g.nD = (c_hi - 1) / kKC - g.d0 + 1;
-    }
     return g;
 }
 
-// Pipelined block-sequential sweep (see the file header).  Roles:
-//   warp 0: TMA producer, warp 1: MMA issuer + TMEM owner,
-//   warps 2-5: drawers (epilogue, redraws, snapshots),
-//   warps 6-9: generators (one-hot and delta operand tiles).
-// Per block kb the MMA consumes nK main chunks (X built from the states
-// after block kb-2's redraw, with block kb-1 still at its old values) and
-// nD delta chunks (+1 at the new, -1 at the old state of every site of block
-// kb-1 that changed), so the accumulator holds the fields of block kb's
-// sites for the states after block kb-1.  Accumulators alternate between
-// two TMEM buffers; snap[kb % 2] holds block kb's states before its redraw.
-__global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant__ CUtensorMap tm_j,
+// One step of a pair's schedule: n K chunks (n0 from c0, then the rest from
+// c1), their kind (main or delta), the blocks whose accumulators they feed
+// (t1 < 0: one), the block whose redraw the generator waits for before the
+// step, the block whose accumulator is complete after it, and the blocks
+// whose changes a delta step carries (d1 < 0: one).
+struct Seg {
+    int n, n0, c0, c1;
+    bool delta;
+    long long t0, t1, wait_kb, commit_kb, d0, d1;
+};
+
+__device__ __forceinline__ int seg_chunk(const Seg &s, int k) { return k < s.n0 ? s.c0 + k : s.c1 + (k - s.n0); }
+
+__device__ __forceinline__ void blk_chunks(const MmaArgs &p, long long kb, int &lo, int &hi)
+{
+    const Blk g = blk_of(p, kb);
+    lo = g.i0 * p.q / kKC;
+    hi = ((g.i0 + g.Bk) * p.q - 1) / kKC;
+}
+
+__device__ Seg seg_info(const MmaArgs &p, long long P, int step)
+{
+    Seg s;
+    s.n = s.n0 = s.c0 = s.c1 = 0;
+    s.delta = false;
+    s.t0 = s.t1 = s.wait_kb = s.commit_kb = s.d0 = s.d1 = -1;
+    const long long b0 = 2 * P, b1 = 2 * P + 1;
+    const bool has0 = b0 < p.nblocks, has1 = b1 < p.nblocks;
+    if (step == 0 || step == 2) {  // main chunks
+        if (!has0) return s;
+        s.c0 = step == 0 ? 0 : p.X;
+        s.n = s.n0 = step == 0 ? p.X : p.nK - p.X;
+        s.t0 = b0;
+        s.t1 = has1 ? b1 : -1;
+        if (step == 2 && P == 0) s.commit_kb = b0;
+        return s;
+    }
+    if (P < 1) return s;
+    s.delta = true;
+    if (step == 1) {  // block 2P-2's changes into block 2P-1
+        if (b0 - 1 >= p.nblocks) return s;
+        int lo, hi;
+        blk_chunks(p, b0 - 2, lo, hi);
+        s.c0 = lo;
+        s.n = s.n0 = hi - lo + 1;
+        s.t0 = b0 - 1;
+        s.d0 = b0 - 2;
+        s.wait_kb = b0 - 2;
+        s.commit_kb = b0 - 1;
+        return s;
+    }
+    if (!has0) return s;  // step 3: blocks 2P-2, 2P-1 into the pair
+    int a0, a1, c0, c1;
+    blk_chunks(p, b0 - 2, a0, a1);
+    blk_chunks(p, b0 - 1, c0, c1);
+    if (c0 <= a1 + 1 && a0 <= c1 + 1) {  // overlapping or adjacent ranges: one run
+        s.c0 = min(a0, c0);
+        s.n = s.n0 = max(a1, c1) - s.c0 + 1;
+    } else {  // the pair of blocks wraps around the end of a sweep
+        s.c0 = a0;
+        s.n0 = a1 - a0 + 1;
+        s.c1 = c0;
+        s.n = s.n0 + (c1 - c0 + 1);
+    }
+    s.t0 = b0;
+    s.t1 = has1 ? b1 : -1;
+    s.d0 = b0 - 2;
+    s.d1 = b0 - 1;
+    s.wait_kb = b0 - 1;
+    s.commit_kb = b0;
+    return s;
+}
+
+// Persistent paired-block sweep (see the file header).
+__global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant__ CUtensorMap tm_j2,
+                                                           const __grid_constant__ CUtensorMap tm_j1,
                                                            const MmaArgs p)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -277,28 +350,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + lay.misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(base + lay.misc + 4);
     // barrier addresses
-    const uint32_t full_a = su32(bars), full_b = full_a + 8 * kNS, empty = full_b + 8 * kNS;
-    const uint32_t acc_full = empty + 8 * kNS;  // [2], one per accumulator buffer
-    const uint32_t acc_empty = acc_full + 16;   // [2]
-    const uint32_t ready = acc_empty + 16;      // [2], states after block kb: barrier kb % 2
-    const uint32_t corr_bar = ready + 16;       // staged coupling blocks of block kb: phase kb
+    const uint32_t full_a = su32(bars), empty_a = full_a + 8 * kNA;
+    const uint32_t full_b = empty_a + 8 * kNA, empty_b = full_b + 8 * kNB;
+    const uint32_t acc_full = empty_b + 8 * kNB;  // [4], accumulator of block kb in slot kb % 4
+    const uint32_t acc_empty = acc_full + 32;     // [4]
+    const uint32_t ready = acc_empty + 32;        // [2], states after block kb: barrier kb % 2
+    const uint32_t corr_bar = ready + 16;         // staged coupling blocks of block kb: phase kb
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = p.q, L = p.L, NC = p.NC, Lp = p.Lp;
-    const int Sst = st_stride(Lp);
+    const int Sst = st_stride(Lp), Ssn = snap_stride(p.B);
     const size_t cta0 = (size_t)blockIdx.x * NC;
-    const long long nblocks = (long long)p.nsweeps * p.nb;
+    const long long nblocks = p.nblocks;
+    const long long npairs = (nblocks + 1) / 2;  // the schedule runs P = 0 .. npairs (tail)
+    // snapshot of block kb (its states before its redraw): pair slot (kb/2)%2, block kb%2
+    auto snap_of = [&](long long kb) { return snap + (size_t)((((kb >> 1) & 1) * 2 + (kb & 1)) * NC) * Ssn; };
 
     if (tid == 0) {
-        for (int s = 0; s < kNS; ++s) {
+        for (int s = 0; s < kNA; ++s) {
             mbar_init(full_a + 8 * s, 1);
-            mbar_init(full_b + 8 * s, 4);
-            mbar_init(empty + 8 * s, 1);
+            mbar_init(empty_a + 8 * s, 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int s = 0; s < kNB; ++s) {
+            mbar_init(full_b + 8 * s, 4);
+            mbar_init(empty_b + 8 * s, 1);
+        }
+        for (int b = 0; b < 4; ++b) {
             mbar_init(acc_full + 8 * b, 1);
             mbar_init(acc_empty + 8 * b, 4);
-            mbar_init(ready + 8 * b, 4);
         }
+        mbar_init(ready, 4);
+        mbar_init(ready + 8, 4);
         mbar_init(corr_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -314,17 +395,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
         const size_t m = cta0 + c;
         st[c * Sst + x] = (m < (size_t)p.M && x < L) ? p.states[m * L + x] : 0;
     }
-    for (int c = tid; c < p.nK; c += kThreads) {  // sites touched by main chunk c
+    for (int c = tid; c < p.nK; c += kThreads) {  // sites touched by K chunk c
         const int k0 = c * kKC;
-        jtab[2 * c] = (unsigned short)(k0 / q);
+        jtab[2 * c] = (unsigned short)min(L - 1, k0 / q);
         jtab[2 * c + 1] = (unsigned short)min(L - 1, (k0 + kKC - 1) / q);
     }
     __syncthreads();
-    {   // snapshot of block 0
-        const int B0 = min(p.B, L);
-        for (int k = tid; k < NC * B0; k += kThreads) {
-            const int c = k / B0, x = k - c * B0;
-            snap[c * kSnapStride + x] = st[c * Sst + x];
+    for (long long kb = 0; kb < 2 && kb < nblocks; ++kb) {  // snapshots of pair 0
+        const Blk g = blk_of(p, kb);
+        uint8_t *sn = snap_of(kb);
+        for (int k = tid; k < NC * g.Bk; k += kThreads) {
+            const int c = k / g.Bk, x = k - c * g.Bk;
+            sn[c * Ssn + x] = st[c * Sst + g.i0 + x];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -335,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
     // Stage the coupling blocks J_ij (i, j in block kb, j < i) for the
     // in-block corrections: one bulk copy per block of bs floats.
     auto stage_corr = [&](long long kb) {
-        const BlockGeo g = block_geo(p, kb);
+        const Blk g = blk_of(p, kb);
         const uint32_t bytes = (uint32_t)(g.Bk * (g.Bk - 1) / 2) * (uint32_t)p.bs * 4u;
         mbar_expect_tx(corr_bar, bytes);
         int slot = 0;
@@ -348,30 +430,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
-            long long t = 0;
-            int s = 0, lap = 0;  // t = lap * kNS + s
+            long long issued = 0;
+            int sa = 0, lap = 0;  // ring slot and lap of the next coupling tile
             bool ok = true;
-            for (long long kb = 0; kb < nblocks && ok; ++kb) {
-                const BlockGeo g = block_geo(p, kb);
-                for (int c = 0; c < p.nK + g.nD; ++c, ++t) {
-                    if (lap > 0 && !mbar_wait(empty + 8 * s, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
-                        ok = false;
-                        break;
-                    }
-                    const int x = (c < p.nK ? c : g.d0 + (c - p.nK)) * kKC;
-                    mbar_expect_tx(full_a + 8 * s, 2 * kTileA);
-                    // one op: slabs (hi, lo) of K chunk x/64 for 128 rows
-                    tma_load_3d(su32(base + lay.a + s * 2 * kTileA), &tm_j, 0, g.i0 * q, 2 * (x / kKC), full_a + 8 * s);
-                    if (++s == kNS) {
-                        s = 0;
-                        ++lap;
+            for (long long P = 0; P <= npairs && ok; ++P)
+                for (int step = 0; step < 4 && ok; ++step) {
+                    const Seg sg = seg_info(p, P, step);
+                    for (int k = 0; k < sg.n && ok; ++k) {
+                        const int c = seg_chunk(sg, k);
+                        if (lap > 0 && !mbar_wait(empty_a + 8 * sa, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        const int nt = sg.t1 >= 0 ? 2 : 1;
+                        const int r0 = (int)(sg.t0 % p.nb) * kRowsA, r1 = (int)((sg.t1 >= 0 ? sg.t1 : 0) % p.nb) * kRowsA;
+                        const uint32_t dst = su32(base + lay.a + sa * kSlotA), bar = full_a + 8 * sa;
+                        mbar_expect_tx(bar, (uint32_t)nt * 2 * kTileA);
+                        if (nt == 2 && r1 == r0 + kRowsA) {
+                            // one op: hi and lo slabs of K chunk c for both blocks' 256 rows
+                            tma_load_3d(dst, &tm_j2, 0, r0, 2 * c, bar);
+                        } else {
+                            for (int u = 0; u < nt; ++u) {
+                                const int r = u == 0 ? r0 : r1;
+                                tma_load_3d(dst + u * kTileA, &tm_j1, 0, r, 2 * c, bar);                // hi
+                                tma_load_3d(dst + (2 + u) * kTileA, &tm_j1, 0, r, 2 * c + 1, bar);      // lo
+                            }
+                        }
+                        ++issued;
+                        if (++sa == kNA) {
+                            sa = 0;
+                            ++lap;
+                        }
                     }
                 }
-            }
             if (*abort_flag) {
                 volatile int no_abort = 0;
-                for (long long u = t > kNS ? t - kNS : 0; u < t; ++u)
-                    mbar_wait(full_a + 8 * (int)(u % kNS), (uint32_t)((u / kNS) & 1), &no_abort, p.err);
+                for (long long u = issued > kNA ? issued - kNA : 0; u < issued; ++u)
+                    mbar_wait(full_a + 8 * (int)(u % kNA), (uint32_t)((u / kNA) & 1), &no_abort, p.err);
             }
         }
     } else if (warp == 1) {
@@ -379,42 +474,58 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
         if (lane == 0) {
             // kind::f16: D F32 (bit 4), A = B = F16 (0), K-major, N >> 3 at 17, M >> 4 at 24.
             const uint32_t idesc = (1u << 4) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kRowsA >> 4) << 24);
-            int s = 0;
-            uint32_t ph = 0;  // stage and phase parity of the current chunk
+            int sa = 0, sb = 0;
+            uint32_t pha = 0, phb = 0;
             bool ok = true;
-            for (long long kb = 0; kb < nblocks && ok; ++kb) {
-                const BlockGeo g = block_geo(p, kb);
-                const int buf = (int)(kb & 1);
-                if (kb >= 2 && !mbar_wait(acc_empty + 8 * buf, (uint32_t)(((kb - 2) >> 1) & 1), abort_flag, p.err)) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t dcol = tmem + (uint32_t)buf * p.acc_stride;
-                for (int c = 0; c < p.nK + g.nD; ++c) {
-                    if (!mbar_wait(full_a + 8 * s, ph, abort_flag, p.err) ||
-                        !mbar_wait(full_b + 8 * s, ph, abort_flag, p.err)) {
-                        ok = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t ah = su32(base + lay.a + s * 2 * kTileA), al = ah + kTileA;
-                    const uint32_t bb = su32(base + lay.b + s * NC * 128);
+            for (long long P = 0; P <= npairs && ok; ++P)
+                for (int step = 0; step < 4 && ok; ++step) {
+                    const Seg sg = seg_info(p, P, step);
+                    for (int k = 0; k < sg.n && ok; ++k) {
+                        const int c = seg_chunk(sg, k);
+                        const bool first = !sg.delta && c == 0;  // first chunk of the pair's accumulators
+                        if (!mbar_wait(full_b + 8 * sb, phb, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        if (!mbar_wait(full_a + 8 * sa, pha, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t bb = su32(base + lay.b + sb * NC * 128);
+                        const uint32_t slot_a = su32(base + lay.a + sa * kSlotA);
+                        for (int u = 0; u < 2; ++u) {
+                            const long long tb = u == 0 ? sg.t0 : sg.t1;
+                            if (tb < 0) continue;
+                            if (first && tb >= 4 &&
+                                !mbar_wait(acc_empty + 8 * (int)(tb & 3), (uint32_t)(((tb - 4) >> 2) & 1), abort_flag,
+                                           p.err)) {
+                                ok = false;
+                                break;
+                            }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t dcol = tmem + (uint32_t)(tb & 3) * p.acc_stride;
+                            const uint32_t ah = slot_a + u * kTileA, al = slot_a + (2 + u) * kTileA;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t bd = desc_noswz(bb + kk * 256);
-                        mma_f16(dcol, desc_sw128(ah + kk * 32), bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-                        mma_f16(dcol, desc_sw128(al + kk * 32), bd, idesc, 1u);
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t bd = desc_noswz(bb + kk * 256);
+                                mma_f16(dcol, desc_sw128(ah + kk * 32), bd, idesc, (first && kk == 0) ? 0u : 1u);
+                                mma_f16(dcol, desc_sw128(al + kk * 32), bd, idesc, 1u);
+                            }
+                        }
+                        if (!ok) break;
+                        mma_commit(empty_a + 8 * sa);
+                        if (++sa == kNA) {
+                            sa = 0;
+                            pha ^= 1u;
+                        }
+                        mma_commit(empty_b + 8 * sb);
+                        if (++sb == kNB) {
+                            sb = 0;
+                            phb ^= 1u;
+                        }
                     }
-                    mma_commit(empty + 8 * s);
-                    if (++s == kNS) {
-                        s = 0;
-                        ph ^= 1u;
-                    }
+                    if (ok && sg.commit_kb >= 0) mma_commit(acc_full + 8 * (int)(sg.commit_kb & 3));
                 }
-                if (!ok) break;
-                mma_commit(acc_full + 8 * buf);
-            }
         }
     } else if (warp < 6) {
         // ------------------------------------------------------------ drawers (warps 2-5)
@@ -432,38 +543,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
             staged = 1;
         }
         for (long long kb = 0; kb < nblocks; ++kb) {
-            const BlockGeo g = block_geo(p, kb);
-            const int buf = (int)(kb & 1);
+            const Blk g = blk_of(p, kb);
+            const int slot = (int)(kb & 3);
             const uint64_t sweep = p.sweep0 + (uint64_t)(kb / p.nb);
-            if (ok && !mbar_wait(acc_full + 8 * buf, (uint32_t)((kb >> 1) & 1), abort_flag, p.err)) ok = false;
+            if (ok && !mbar_wait(acc_full + 8 * slot, (uint32_t)((kb >> 2) & 1), abort_flag, p.err)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int c0 = 0; c0 < NC && ok; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)buf * p.acc_stride + (uint32_t)c0, v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int e = 0; e < 16; ++e) Hs[row * HsStride + c0 + e] = __uint_as_float(v[e]);
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty + 8 * buf);
             for (int k = w; k < g.Bk * q; k += 128) hrow[k] = p.h[(size_t)g.i0 * q + k];
             if (ok && !mbar_wait(corr_bar, (uint32_t)(kb & 1), abort_flag, p.err)) ok = false;
             named_bar(1, 128);
-            if (*abort_flag) ok = false;
-            // --- sequential redraw of block kb, one thread per chain
-            const uint8_t *old = snap + buf * NC * kSnapStride;
-            for (int ch = w; ch < NC && ok; ch += 128) {
-                const uint64_t m = cta0 + ch;
-                for (int pp = 0; pp < g.Bk; ++pp) {
-                    const int i = g.i0 + pp;
+            if (*abort_flag) ok = false;  // uniform from here on
+            // --- sequential redraw of block kb, one site at a time, one thread per chain
+            const uint8_t *old = snap_of(kb);
+            const uint32_t tacc = tmem + ((uint32_t)lane_base << 16) + (uint32_t)slot * p.acc_stride;
+            for (int pp = 0; pp < g.Bk && ok; ++pp) {
+                // accumulator rows [pp*q, pp*q + q) of the warps whose lanes hold them -> Hs[a][chain]
+                const int r0 = pp * q;
+                if (lane_base < r0 + q && lane_base + 32 > r0) {
+                    for (int c0 = 0; c0 < NC; c0 += 16) {
+                        uint32_t v[16];
+                        tmem_ld16(tacc + (uint32_t)c0, v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (row >= r0 && row < r0 + q) {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) Hs[(row - r0) * HsStride + c0 + e] = __uint_as_float(v[e]);
+                        }
+                    }
+                }
+                named_bar(1, 128);
+                const int i = g.i0 + pp;
+                for (int ch = w; ch < NC; ch += 128) {
+                    const uint64_t m = cta0 + ch;
                     float H[32];
 #pragma unroll
                     for (int a = 0; a < 32; ++a)
-                        if (a < q) H[a] = hrow[pp * q + a] + Hs[(pp * q + a) * HsStride + ch];
+                        if (a < q) H[a] = hrow[pp * q + a] + Hs[a * HsStride + ch];
                     const float *cb = corr + (uint32_t)(pp * (pp - 1) / 2) * blkb;  // blocks (i, j < i)
                     for (int jj = 0; jj < pp; ++jj) {
-                        const int sn = st[ch * Sst + g.i0 + jj], so = old[ch * kSnapStride + jj];
+                        const int sn = st[ch * Sst + g.i0 + jj], so = old[ch * Ssn + jj];
                         if (sn == so) continue;
                         const float *rn = cb + jj * blkb + sn * q, *ro = cb + jj * blkb + so * q;
 #pragma unroll
@@ -492,23 +608,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                         if (a < q && thr < H[a]) pick = a;
                     st[ch * Sst + i] = (uint8_t)pick;
                 }
+                named_bar(1, 128);  // Hs is rewritten for the next site
             }
-            // snapshot of the next block's states before its redraw
-            if (ok && kb + 1 < nblocks) {
-                const BlockGeo gn = block_geo(p, kb + 1);
-                uint8_t *nsnap = snap + (buf ^ 1) * NC * kSnapStride;
-                for (int k = w; k < NC * gn.Bk; k += 128) {
-                    const int ch = k / gn.Bk, x = k - ch * gn.Bk;
-                    nsnap[ch * kSnapStride + x] = st[ch * Sst + gn.i0 + x];
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + 8 * slot);
+            // after an odd block: snapshots of the next pair's blocks before their redraw
+            if (ok && (kb & 1))
+                for (long long nb2 = kb + 1; nb2 <= kb + 2 && nb2 < nblocks; ++nb2) {
+                    const Blk gn = blk_of(p, nb2);
+                    uint8_t *sn = snap_of(nb2);
+                    for (int k = w; k < NC * gn.Bk; k += 128) {
+                        const int ch = k / gn.Bk, x = k - ch * gn.Bk;
+                        sn[ch * Ssn + x] = st[ch * Sst + gn.i0 + x];
+                    }
                 }
-            }
             named_bar(1, 128);
             // the staged blocks are free again: stage the next block's
             if (w == 0 && ok && !*abort_flag && kb + 1 < nblocks) {
                 stage_corr(kb + 1);
                 ++staged;
             }
-            if (lane == 0) mbar_arrive(ready + 8 * buf);
+            if (lane == 0) mbar_arrive(ready + 8 * (int)(kb & 1));
         }
         if (!ok) *abort_flag = 1;
         if (w == 0 && *abort_flag && staged > 0) {
@@ -520,69 +641,85 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
         // Thread w owns the operand row of chain w (NC <= 128): per K chunk it
         // zeroes the row (8 x 16-byte stores) and then stores the few nonzero
         // halfwords (same thread, so program order keeps the stores ordered).
-        // A main chunk holds +1 at (j, s_j) for the sites j it overlaps; a
-        // delta chunk holds +1 at (j, new s_j) and -1 at (j, old s_j) for the
-        // changed sites of the previous block.
         const int w = tid - 192;  // 0..127
         const bool own = w < NC;
         unsigned char *const row0 = base + lay.b + noswz_off(own ? w : 0, 0);
         const uint8_t *const strow = st + (own ? w : 0) * Sst;
-        int s = 0, lap = 0;  // stage and ring lap of the current chunk
+        const int wrow = (own ? w : 0) * Ssn;
+        int sb = 0, lap = 0;  // ring slot and lap of the current chunk
         bool ok = true;
-        for (long long kb = 0; kb < nblocks && ok; ++kb) {
-            const BlockGeo g = block_geo(p, kb);
-            const int buf = (int)(kb & 1);
-            // main chunks need the states after block kb-2; block kb-1 from its snapshot
-            if (kb >= 2 && !mbar_wait(ready + 8 * buf, (uint32_t)(((kb - 2) >> 1) & 1), abort_flag, p.err)) {
-                ok = false;
-                break;
+        for (long long P = 0; P <= npairs && ok; ++P) {
+            // main chunks: blocks 2P-2 and 2P-1 from their snapshots (pair slot (P-1)%2)
+            int s0lo = L, s0hi = L, s1lo = L, s1hi = L;
+            const uint8_t *ps0 = snap, *ps1 = snap;
+            if (P >= 1) {
+                const Blk g0 = blk_of(p, 2 * P - 2), g1 = blk_of(p, 2 * P - 1);
+                s0lo = g0.i0;
+                s0hi = g0.i0 + g0.Bk;
+                s1lo = g1.i0;
+                s1hi = g1.i0 + g1.Bk;
+                ps0 = snap_of(2 * P - 2) + wrow;
+                ps1 = snap_of(2 * P - 1) + wrow;
             }
-            const uint8_t *psrow = snap + (buf ^ 1) * NC * kSnapStride + (own ? w : 0) * kSnapStride;
-            const int pi0 = kb > 0 ? g.pi0 : L, pi1 = kb > 0 ? g.pi0 + g.pBk : L;  // block kb-1's sites
-            for (int c = 0; c < p.nK + g.nD; ++c) {
-                const bool delta = c >= p.nK;
-                if (c == p.nK &&
-                    !mbar_wait(ready + 8 * (buf ^ 1), (uint32_t)(((kb - 1) >> 1) & 1), abort_flag, p.err)) {
+            for (int step = 0; step < 4 && ok; ++step) {
+                const Seg sg = seg_info(p, P, step);
+                if (sg.n > 0 && sg.wait_kb >= 0 &&
+                    !mbar_wait(ready + 8 * (int)(sg.wait_kb & 1), (uint32_t)((sg.wait_kb >> 1) & 1), abort_flag,
+                               p.err)) {
                     ok = false;
                     break;
                 }
-                if (lap > 0 && !mbar_wait(empty + 8 * s, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
-                    ok = false;
-                    break;
-                }
-                const int k0 = (delta ? g.d0 + (c - p.nK) : c) * kKC;
-                unsigned char *rowp = row0 + s * NC * 128;
-                if (own) {
+                for (int k = 0; k < sg.n; ++k) {
+                    if (lap > 0 && !mbar_wait(empty_b + 8 * sb, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    const int c = seg_chunk(sg, k);
+                    const int k0 = c * kKC;
+                    unsigned char *rowp = row0 + sb * NC * 128;
+                    if (own) {
 #pragma unroll
-                    for (int pc = 0; pc < 8; ++pc)
-                        *reinterpret_cast<uint4 *>(rowp + pc * 128) = make_uint4(0, 0, 0, 0);
-                    if (!delta) {
-                        const int jlo = jtab[2 * c], jhi = jtab[2 * c + 1];
-                        for (int j = jlo; j <= jhi; ++j) {
-                            const int sj = (j >= pi0 && j < pi1) ? psrow[j - pi0] : strow[j];
-                            const int pos = j * q + sj - k0;
-                            if (pos >= 0 && pos < kKC)
-                                *reinterpret_cast<unsigned short *>(rowp + (pos >> 3) * 128 + (pos & 7) * 2) = 0x3c00u;
-                        }
-                    } else {
-                        for (int x = 0; x < g.pBk; ++x) {
-                            const int j = g.pi0 + x;
-                            const int sn = strow[j], so = psrow[x];
-                            if (sn == so) continue;
-                            const int pn = j * q + sn - k0, po = j * q + so - k0;
-                            if (pn >= 0 && pn < kKC)
-                                *reinterpret_cast<unsigned short *>(rowp + (pn >> 3) * 128 + (pn & 7) * 2) = 0x3c00u;
-                            if (po >= 0 && po < kKC)
-                                *reinterpret_cast<unsigned short *>(rowp + (po >> 3) * 128 + (po & 7) * 2) = 0xbc00u;
+                        for (int pc = 0; pc < 8; ++pc)
+                            *reinterpret_cast<uint4 *>(rowp + pc * 128) = make_uint4(0, 0, 0, 0);
+                        if (!sg.delta) {
+                            const int jlo = jtab[2 * c], jhi = jtab[2 * c + 1];
+                            for (int j = jlo; j <= jhi; ++j) {
+                                const int sj = (j >= s0lo && j < s0hi)   ? ps0[j - s0lo]
+                                               : (j >= s1lo && j < s1hi) ? ps1[j - s1lo]
+                                                                         : strow[j];
+                                const int pos = j * q + sj - k0;
+                                if (pos >= 0 && pos < kKC)
+                                    *reinterpret_cast<unsigned short *>(rowp + (pos >> 3) * 128 + (pos & 7) * 2) =
+                                        0x3c00u;
+                            }
+                        } else {
+                            for (int u = 0; u < 2; ++u) {
+                                const long long db = u == 0 ? sg.d0 : sg.d1;
+                                if (db < 0) continue;
+                                const Blk gd = blk_of(p, db);
+                                const uint8_t *po = (u == 0 ? ps0 : ps1);  // d0 = 2P-2, d1 = 2P-1
+                                for (int x = 0; x < gd.Bk; ++x) {
+                                    const int j = gd.i0 + x;
+                                    const int sn = strow[j], so = po[x];
+                                    if (sn == so) continue;
+                                    const int pn = j * q + sn - k0, pd = j * q + so - k0;
+                                    if (pn >= 0 && pn < kKC)
+                                        *reinterpret_cast<unsigned short *>(rowp + (pn >> 3) * 128 + (pn & 7) * 2) =
+                                            0x3c00u;
+                                    if (pd >= 0 && pd < kKC)
+                                        *reinterpret_cast<unsigned short *>(rowp + (pd >> 3) * 128 + (pd & 7) * 2) =
+                                            0xbc00u;
+                                }
+                            }
                         }
                     }
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(full_b + 8 * s);
-                if (++s == kNS) {
-                    s = 0;
-                    ++lap;
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(full_b + 8 * sb);
+                    if (++sb == kNB) {
+                        sb = 0;
+                        ++lap;
+                    }
                 }
             }
         }
@@ -604,20 +741,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
     }
 }
 
-// Jt[L*q rows (i,a)][Kp/64 slabs][2 (hi, lo)][64] fp16: for column
-// k = (j,b) of slab k/64, hi = fp16(J_ij(a,b)) and lo = fp16(J_ij(a,b) - hi)
-// (J_ij(a,b) = J[i][j][a][b]); zero padding beyond L*q columns.  Each row
-// interleaves the hi and lo slabs so one 3-D TMA op brings both.
-__global__ void k_build_mma_layout(const float *__restrict__ J, __half *__restrict__ jt, int L, int q, int Kp)
+// Jt[nb*128 rows][Kp/64 slabs][2 (hi, lo)][64] fp16.  Row blk*128 + pp*q + a
+// holds site i = blk*B + pp, symbol a (pp < sites of the block; the other
+// rows of the 128 are zero); for column k = (j,b) of slab k/64,
+// hi = fp16(J_ij(a,b)) and lo = fp16(J_ij(a,b) - hi) (J_ij(a,b) = J[i][j][a][b]);
+// zero beyond L*q columns.  Each row interleaves the hi and lo slabs so one
+// 3-D TMA op brings both.
+__global__ void k_build_mma_layout(const float *__restrict__ J, __half *__restrict__ jt, int L, int q, int Kp, int B,
+                                   int nb)
 {
-    const size_t rows = (size_t)L * q, n = rows * Kp;
+    const size_t rows = (size_t)nb * kRowsA, n = rows * Kp;
     const int Q = L * q;
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
         const size_t r = t / Kp;
         const int k = (int)(t - r * Kp);
+        const int blk = (int)(r / kRowsA), rr = (int)(r % kRowsA);
+        const int pp = rr / q, a = rr % q, i = blk * B + pp;
         float v = 0.0f;
-        if (k < Q) {
-            const int i = (int)(r / q), a = (int)(r % q), j = k / q, b = k % q;
+        if (k < Q && pp < B && i < L) {
+            const int j = k / q, b = k % q;
             v = J[(((size_t)i * L + j) * q + a) * q + b];
         }
         const __half vh = __float2half_rn(v);
@@ -648,15 +790,16 @@ EncodeTiledFn encode_fn()
 
 // 3-D view of Jt: dim 0 = 64 elements of a slab (contiguous), dim 1 = row
 // (stride 2*Kp*2 bytes), dim 2 = slab index 2*(k/64) + {0 hi, 1 lo} (stride
-// 128 bytes).  Box {64, 128, 2}: one op lands the hi tile and then the lo
-// tile of a K chunk for 128 rows, each a 128B-swizzled 128 x 64 tile.
-int make_map(CUtensorMap *map, const __half *ptr, int rows, int Kp)
+// 128 bytes), 128B swizzle.  box_rows x box_slabs per op: {256, 2} lands
+// the hi tiles of two consecutive blocks and then their lo tiles; {128, 1}
+// one tile.
+int make_map(CUtensorMap *map, const __half *ptr, int rows, int Kp, int box_rows, int box_slabs)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return bm_fail(BM_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
     cuuint64_t dims[3] = {(cuuint64_t)kKC, (cuuint64_t)rows, (cuuint64_t)(2 * Kp / kKC)};
     cuuint64_t strides[2] = {(cuuint64_t)Kp * 4, (cuuint64_t)kKC * 2};
-    cuuint32_t box[3] = {(cuuint32_t)kKC, (cuuint32_t)kRowsA, 2};
+    cuuint32_t box[3] = {(cuuint32_t)kKC, (cuuint32_t)box_rows, (cuuint32_t)box_slabs};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<__half *>(ptr), dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -665,19 +808,29 @@ int make_map(CUtensorMap *map, const __half *ptr, int rows, int Kp)
     return BM_OK;
 }
 
+// Sites per block: as many as fill the 128 accumulator rows (at most kBmax),
+// but at least two blocks per sweep, so that the two blocks of a pair never
+// hold the same sites.
+int block_sites(int L, int q)
+{
+    int B = std::min(kBmax, kRowsA / q);
+    if ((L + B - 1) / B < 2) B = (L + 1) / 2;
+    return B;
+}
+
 }  // namespace
 
 // Chains per CTA for the tensor-core sweep (multiple of 16, <= 128), or 0
-// when the shape does not fit one CTA's shared memory.
+// when the shape does not fit one CTA's shared memory or L < 2.
 int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M)
 {
-    if (m->L > 65535) return 0;  // site indices of the chunk table are 16-bit
+    if (m->L < 2 || m->L > 65535) return 0;  // two blocks per sweep; 16-bit site indices
     const int nsm = m->num_sms > 0 ? m->num_sms : 1;
     int nc = (M + nsm - 1) / nsm;
     nc = std::max(16, (nc + 15) & ~15);
     nc = std::min(nc, 128);  // one operand-row generator thread per chain
     const int Lp = (m->L + 15) & ~15;
-    const int B = std::min(kBmax, kRowsA / m->q);
+    const int B = block_sites(m->L, m->q);
     const int nK = (m->L * m->q + kKC - 1) / kKC;
     while (nc >= 16 && smem_layout(nc, Lp, B, m->bs, nK).total + 1024 > 227 * 1024) nc -= 16;
     return nc >= 16 ? nc : 0;
@@ -685,17 +838,20 @@ int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M)
 
 int bm_mma_prepare(bm_model_s *m, cudaStream_t st)
 {
-    const int rows = m->L * m->q;
-    const int Kp = (rows + kKC - 1) / kKC * kKC;
+    const int B = block_sites(m->L, m->q), nb = (m->L + B - 1) / B;
+    const int rows = nb * kRowsA;  // every block padded to 128 rows
+    const int Kp = (m->L * m->q + kKC - 1) / kKC * kKC;
     if (!m->Jt) {
         m->Kp = Kp;
         BM_CK(cudaMalloc(&m->Jt, (size_t)rows * Kp * 2 * sizeof(__half)));
-        const int rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_j), (const __half *)m->Jt, rows, Kp);
+        int rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_j), (const __half *)m->Jt, rows, Kp, 2 * kRowsA, 2);
+        if (rc == BM_OK)
+            rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_j1), (const __half *)m->Jt, rows, Kp, kRowsA, 1);
         if (rc != BM_OK) return rc;
     }
     const size_t n = (size_t)rows * Kp;
     const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 64);
-    k_build_mma_layout<<<grid, 256, 0, st>>>(m->J, (__half *)m->Jt, m->L, m->q, Kp);
+    k_build_mma_layout<<<grid, 256, 0, st>>>(m->J, (__half *)m->Jt, m->L, m->q, Kp, B, nb);
     BM_CK_LAUNCH("k_build_mma_layout");
     m->mma_current = true;
     return BM_OK;
@@ -722,18 +878,21 @@ int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, 
     a.q = c->q;
     a.Lp = (c->L + 15) & ~15;
     a.bs = m->bs;
-    a.B = std::min(kBmax, kRowsA / c->q);
+    a.B = block_sites(c->L, c->q);
     a.nb = (c->L + a.B - 1) / a.B;
     a.nK = m->Kp / kKC;
     a.NC = NC;
     a.nsweeps = nsweeps;
-    a.acc_stride = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;
-    a.tmem_cols = 2 * a.acc_stride;  // two accumulators
+    a.nblocks = (long long)nsweeps * a.nb;
+    a.X = a.nK / 2;  // main chunks before the previous pair's first delta step
+    a.acc_stride = NC <= 32 ? 32 : NC <= 64 ? 64 : 128;
+    a.tmem_cols = 4 * a.acc_stride;  // four accumulators
     const Smem lay = smem_layout(NC, a.Lp, a.B, a.bs, a.nK);
     const size_t smem = lay.total + 1024;
     BM_CK(cudaFuncSetAttribute(k_gibbs_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (c->M + NC - 1) / NC;
-    k_gibbs_mma<<<grid, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(m->tmap_j), a);
+    k_gibbs_mma<<<grid, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(m->tmap_j),
+                                              *reinterpret_cast<const CUtensorMap *>(m->tmap_j1), a);
     BM_CK_LAUNCH("k_gibbs_mma");
     return BM_OK;
 }
