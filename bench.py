@@ -330,6 +330,16 @@ def run_ours(args, rank, world, local):
                         "launch / CUDA-event launch time; peak: " + peak_src +
                         "; fp16 and bf16 share the dense rate"}
 
+    # ---- roofline of the chain counts (the other tensor-core row of the step):
+    # one-hot X^T X over the upper block triangle, 2*M*(L(L+1)/2)*q^2 flops,
+    # FP8 operands; peak = the measured bf16 rate x 2 (nominal fp8/bf16 ratio).
+    cs_flops = 2.0 * M_CHAINS * (L_SITES * (L_SITES + 1) / 2) * Q * Q
+    cs_ach = cs_flops / (rows["chain_stats_ms"] * 1e-3) / 1e12
+    roofline_counts = {"bound": "tensor", "achieved": cs_ach, "peak": 2 * peak_tf, "unit": "TFLOP/s",
+                       "frac": cs_ach / (2 * peak_tf), "kernel": "k_onehot_t + k_counts_tc",
+                       "note": "achieved = 2*M*(L(L+1)/2)*q^2 flops / CUDA-event time of bm_chain_stats "
+                               "(one-hot build included); peak: fp8 = 2 x " + peak_src}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n = args.cpu_chains or calibrate_oracle_chains(15.0)
@@ -339,9 +349,9 @@ def run_ours(args, rank, world, local):
                          f"{dt:.1f} s, FP64 C, 1 thread"}
 
     # Kernels launched per step: J tensor-core layout rebuild (the previous
-    # update changed J) + Gibbs sweep, chain counts, update (pairs, fields,
-    # Pearson partial sum) + gather-layout rebuild.
-    launches_per_step = 2 + 1 + 3 + 1
+    # update changed J) + Gibbs sweep, chain counts (one-hot build + product),
+    # update (pairs, fields, Pearson partial sum) + gather-layout rebuild.
+    launches_per_step = 2 + 2 + 3 + 1
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -356,7 +366,7 @@ def run_ours(args, rank, world, local):
                                "ms_per_step": ms_plain, "gibbs_ms_per_sweep": ms_plain_gibbs / NSWEEPS,
                                "engine": "CUDA-core FP32 gather (k_gibbs_staged)",
                                "speedup_of_value": ms_plain / ms_step},
-                "roofline": roofline, "cpu_baseline": cpu,
+                "roofline": roofline, "roofline_chain_stats": roofline_counts, "cpu_baseline": cpu,
                 "e2e": {"value": world * site_updates_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps,

@@ -162,14 +162,18 @@ int bm_model_set_engine(bm_model m, int engine);
 
 /* Kernel form used by bm_chain_stats (bm_chains_set_stats_engine). */
 enum {
-    BM_STATS_AUTO = 0,      /* default: the fastest measured form (currently BM_STATS_SIMT) */
+    BM_STATS_AUTO = 0,      /* default: the fastest measured form (BM_STATS_MMA_FP8 when M < 2^24,
+                               else BM_STATS_SIMT) */
     BM_STATS_SIMT = 1,      /* CUDA cores, shared-memory histograms */
-    BM_STATS_MMA_BF16 = 2,  /* tensor cores, BF16 one-hot operands */
-    BM_STATS_MMA_FP8 = 3    /* tensor cores, FP8 E4M3 one-hot operands */
+    BM_STATS_MMA_BF16 = 2,  /* tensor cores, BF16 one-hot operands built in shared memory */
+    BM_STATS_MMA_FP8 = 3    /* tensor cores, FP8 E4M3 one-hot X^T written once to device memory
+                               (L*q x M rounded up to 256 bytes, owned by the chains handle) and
+                               streamed by TMA */
 };
 
 /* Select the bm_chain_stats kernel form for these chains (all forms give
- * identical, exact counts).  BM_EINVAL for an unknown engine. */
+ * identical, exact counts; the tensor-core forms need M < 2^24 and fall back
+ * to BM_STATS_SIMT otherwise).  BM_EINVAL for an unknown engine. */
 int bm_chains_set_stats_engine(bm_chains c, int engine);
 
 /* Synchronise `stream` and report device-side errors recorded by earlier

@@ -250,6 +250,7 @@ int bm_chains_free(bm_chains c)
     if (!c) return BM_OK;
     cudaFree(c->s);
     cudaFree(c->derr);
+    if (c->xt) cudaFree(c->xt);
     delete c;
     return BM_OK;
 }
@@ -347,10 +348,11 @@ int bm_chain_stats(bm_chains c, int32_t *counts_dev, void *stream)
     case BM_STATS_MMA_BF16:
         if (mma_ok) return bm_launch_chain_stats_mma(c->s, c->M, c->L, c->q, counts_dev, 2, c->derr, st);
         break;
+    case BM_STATS_AUTO:  // the TMA-fed FP8 product is the faster form when its FP32 counts are exact
     case BM_STATS_MMA_FP8:
-        if (mma_ok) return bm_launch_chain_stats_mma(c->s, c->M, c->L, c->q, counts_dev, 1, c->derr, st);
+        if (mma_ok) return bm_launch_chain_stats_tc(c, counts_dev, st);
         break;
-    default:  // BM_STATS_AUTO, BM_STATS_SIMT: the shared-memory histogram form is the faster one
+    default:  // BM_STATS_SIMT
         break;
     }
     return bm_launch_chain_stats(c->s, c->M, c->L, c->q, counts_dev, st);

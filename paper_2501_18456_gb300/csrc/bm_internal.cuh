@@ -49,6 +49,12 @@ struct bm_chains_s {
     uint64_t sweep = 0;    // Philox sweep word of the next sweep
     int stats_engine = BM_STATS_AUTO;
     int *derr = nullptr;   // device error word of this handle's kernels
+    // Transposed FP8 one-hot of the states for the tensor-core counts
+    // (xt_rows x xt_cols bytes, owned) and its two TMA tensor maps.
+    void *xt = nullptr;
+    int xt_rows = 0, xt_cols = 0;
+    alignas(64) unsigned char tmap_a[128] = {};
+    alignas(64) unsigned char tmap_b[128] = {};
 };
 
 // ---------------------------------------------------------------------------
@@ -125,6 +131,7 @@ int bm_launch_chain_stats(const uint8_t *s, int M, int L, int q, int32_t *counts
                           cudaStream_t st);
 int bm_launch_chain_stats_mma(const uint8_t *s, int M, int L, int q, int32_t *counts, int elem_bytes,
                               int *err, cudaStream_t st);
+int bm_launch_chain_stats_tc(bm_chains_s *c, int32_t *counts, cudaStream_t st);
 int bm_launch_seq_weights(const uint8_t *msa, int N, int L, int thr, float *w, int *cnt,
                           double *meff_dev, cudaStream_t st);
 int bm_launch_data_stats(const uint8_t *msa, const float *w, int N, int L, int q, double alpha,
