@@ -67,7 +67,8 @@ enum { BM_HOST = 0, BM_DEVICE = 1 };
 /* Which kernel form bm_gibbs_sweep uses (bm_model_set_engine). */
 enum {
     BM_ENGINE_SIMT = 0,  /* FP32 CUDA-core gather of J rows */
-    BM_ENGINE_AUTO = 1,  /* default: tensor cores when the shape fits, else CUDA cores */
+    BM_ENGINE_AUTO = 1,  /* default: tensor cores when q >= 10 and the shape fits, else CUDA
+                            cores (the measured faster form on each side of the crossover) */
     BM_ENGINE_MMA = 2    /* tensor cores: one-hot x (fp16 hi + fp16 lo) J, FP32 accumulate */
 };
 
@@ -262,7 +263,8 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
 /*
  * bm_energy_score -- DCA energy E(s) of n sequences (Eq. 1; Sec. 4.3: low
  * energy = good sequence).  seqs_dev: device uint8[n][L]; E_dev: device
- * float[n].  FP32 accumulation.
+ * float[n].  FP32 accumulation.  A symbol >= q contributes nothing to its
+ * sequence's energy; the next bm_device_status then returns BM_EINVAL.
  */
 int bm_energy_score(bm_model m, const uint8_t *seqs_dev, int n, float *E_dev, void *stream);
 
@@ -273,6 +275,28 @@ int bm_energy_score(bm_model m, const uint8_t *seqs_dev, int n, float *E_dev, vo
  * dE_dev: device float[L][q].
  */
 int bm_mutant_scan(bm_model m, const uint8_t *wt, int where, float *dE_dev, void *stream);
+
+/* Numerical form of bm_fields. */
+enum {
+    BM_FIELDS_FP32 = 0,    /* CUDA cores: FP32 sum over j ascending */
+    BM_FIELDS_FP16X2 = 1,  /* tensor cores: J = fp16 hi + fp16 lo (round to nearest), FP32
+                              accumulation; the numerics of the tensor-core Gibbs sweep */
+    BM_FIELDS_BF16X2 = 2   /* tensor cores: J = bf16 hi + bf16 lo, FP32 accumulation */
+};
+
+/*
+ * bm_fields -- local fields of n sequences, H[k][i][a] = h_i(a) +
+ * sum_{j != i} J_ij(a, s_j^k): the field whose softmax is the Gibbs
+ * conditional of site i (Sec. 2.1) and from which single-mutant energies
+ * are formed (Sec. 4.4).  seqs_dev: device uint8[n][L]; H_dev: device
+ * float[n][L][q], fully written.  `form` is a BM_FIELDS_* value (BM_EINVAL
+ * otherwise).  A symbol >= q contributes nothing; the next bm_device_status
+ * then returns BM_EINVAL.  The tensor-core forms use stream-ordered scratch
+ * of min(n, 65536) * Kp * 2 bytes (Kp = L*q rounded up to 64) and rebuild
+ * their split copy of J after a parameter change (bm_potts_set, an applied
+ * bm_update).
+ */
+int bm_fields(bm_model m, const uint8_t *seqs_dev, int n, float *H_dev, int form, void *stream);
 
 #ifdef __cplusplus
 }

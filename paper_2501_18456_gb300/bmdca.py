@@ -22,6 +22,7 @@ BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ENUMERIC, BM_ETIMEOUT, BM_EDEVICE, BM_
 BM_HOST, BM_DEVICE = 0, 1
 BM_ENGINE_SIMT, BM_ENGINE_AUTO, BM_ENGINE_MMA = 0, 1, 2
 BM_STATS_AUTO, BM_STATS_SIMT, BM_STATS_MMA_BF16, BM_STATS_MMA_FP8 = 0, 1, 2, 3
+BM_FIELDS_FP32, BM_FIELDS_FP16X2, BM_FIELDS_BF16X2 = 0, 1, 2
 
 # name -> (restype, argtypes); kept in the order of include/bmdca.h
 _P, _I, _U64, _F, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_float, ctypes.c_double
@@ -52,6 +53,7 @@ SIGNATURES = {
     "bm_update": (_I, [_P, _P, _P, _P, _I, _F, _D, _P, _P, _P]),
     "bm_energy_score": (_I, [_P, _P, _I, _P, _P]),
     "bm_mutant_scan": (_I, [_P, _P, _I, _P, _P]),
+    "bm_fields": (_I, [_P, _P, _I, _P, _I, _P]),
 }
 
 
@@ -305,3 +307,10 @@ def bm_mutant_scan(m: Model, wt: torch.Tensor, dE: torch.Tensor, stream=None):
     pw, where = _ptr(wt, torch.uint8, m.L, "wt")
     pd = _dev(dE, torch.float32, m.L * m.q, "dE")
     _check(lib().bm_mutant_scan(m.handle, pw, where, pd, _stream(stream)), "bm_mutant_scan")
+
+
+def bm_fields(m: Model, seqs: torch.Tensor, H: torch.Tensor, form: int = BM_FIELDS_FP32, stream=None):
+    n = seqs.shape[0] if seqs.dim() == 2 else 0
+    ps = _dev(seqs, torch.uint8, n * m.L, "seqs")
+    ph = _dev(H, torch.float32, n * m.L * m.q, "H")
+    _check(lib().bm_fields(m.handle, ps, n, ph, form, _stream(stream)), "bm_fields")

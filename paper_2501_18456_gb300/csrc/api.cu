@@ -31,6 +31,7 @@ void free_model(bm_model_s *m)
     cudaFree(m->J_back);
     cudaFree(m->Jg);
     cudaFree(m->Jt);
+    cudaFree(m->Jt_bf);
     cudaFree(m->dflags);
     cudaFree(m->dred);
     delete m;
@@ -157,6 +158,7 @@ int bm_potts_set(bm_model m, const float *h, const float *J, int where, void *st
     if (J) {
         BM_CK(cudaMemcpyAsync(m->J, J, nJ * sizeof(float), copy_kind(where, BM_DEVICE), st));
         m->mma_current = false;
+        m->bf_current = false;
         return bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
     }
     return BM_OK;
@@ -166,13 +168,12 @@ int bm_device_status(bm_model m, void *stream)
 {
     if (!m) return bm_fail(BM_EINVAL, "bm_device_status: NULL model");
     cudaStream_t st = (cudaStream_t)stream;
-    int word = 0;
-    BM_CK(cudaMemcpyAsync(&word, m->dflags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int word[2] = {0, 0};
+    BM_CK(cudaMemcpyAsync(word, m->dflags + 3, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     BM_CK(cudaStreamSynchronize(st));
-    if (word) {
-        BM_CK(cudaMemsetAsync(m->dflags + 3, 0, sizeof(int), st));
-        return bm_fail(BM_ETIMEOUT, "device wait timed out in a Gibbs launch (error word 0x%x)", word);
-    }
+    if (word[0] || word[1]) BM_CK(cudaMemsetAsync(m->dflags + 3, 0, 2 * sizeof(int), st));
+    if (word[0]) return bm_fail(BM_ETIMEOUT, "device wait timed out in a Gibbs launch (error word 0x%x)", word[0]);
+    if (word[1]) return bm_fail(BM_EINVAL, "a scored sequence held a symbol >= q (it contributed nothing)");
     return BM_OK;
 }
 
@@ -329,8 +330,11 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
     cudaStream_t st = (cudaStream_t)stream;
     for (int done = 0; done < nsweeps;) {
         const int k = nsweeps - done < kMaxSweepsPerLaunch ? nsweeps - done : kMaxSweepsPerLaunch;
+        // AUTO: the tensor-core sweep from q = 10 up (measured crossover between
+        // q = 8 and q = 12 at L = 256: the one-hot contraction does q times the
+        // gather's arithmetic and small alphabets make long sequential blocks).
         const bool mma = m->engine == BM_ENGINE_MMA ||
-                         (m->engine == BM_ENGINE_AUTO && bm_gibbs_mma_chains_per_cta(m, c->M) > 0);
+                         (m->engine == BM_ENGINE_AUTO && m->q >= 10 && bm_gibbs_mma_chains_per_cta(m, c->M) > 0);
         const int rc = mma ? bm_launch_gibbs_mma(m, c, k, beta, st) : bm_launch_gibbs_simt(m, c, k, beta, st);
         if (rc != BM_OK) return rc;
         c->sweep += (uint64_t)k;
@@ -451,6 +455,7 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
         float *t = m->h; m->h = m->h_back; m->h_back = t;
         t = m->J; m->J = m->J_back; m->J_back = t;
         m->mma_current = false;
+        m->bf_current = false;
         rc = bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
         if (rc != BM_OK) return rc;
     }
@@ -462,7 +467,20 @@ int bm_energy_score(bm_model m, const uint8_t *seqs_dev, int n, float *E_dev, vo
 {
     if (!m || (n > 0 && (!seqs_dev || !E_dev))) return bm_fail(BM_EINVAL, "bm_energy_score: NULL argument");
     if (n < 0) return bm_fail(BM_EINVAL, "bm_energy_score: n=%d < 0", n);
-    return bm_launch_energy(m->h, m->J, m->L, m->q, seqs_dev, n, E_dev, (cudaStream_t)stream);
+    return bm_launch_energy(m->h, m->J, m->L, m->q, seqs_dev, n, E_dev, m->dflags + 4, (cudaStream_t)stream);
+}
+
+int bm_fields(bm_model m, const uint8_t *seqs_dev, int n, float *H_dev, int form, void *stream)
+{
+    if (!m || (n > 0 && (!seqs_dev || !H_dev))) return bm_fail(BM_EINVAL, "bm_fields: NULL argument");
+    if (n < 0) return bm_fail(BM_EINVAL, "bm_fields: n=%d < 0", n);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (form) {
+    case BM_FIELDS_FP32: return bm_launch_fields_simt(m, seqs_dev, n, H_dev, st);
+    case BM_FIELDS_FP16X2: return bm_launch_fields_tc(m, seqs_dev, n, H_dev, 0, st);
+    case BM_FIELDS_BF16X2: return bm_launch_fields_tc(m, seqs_dev, n, H_dev, 1, st);
+    default: return bm_fail(BM_EINVAL, "bm_fields: unknown form %d", form);
+    }
 }
 
 int bm_mutant_scan(bm_model m, const uint8_t *wt, int where, float *dE_dev, void *stream)

@@ -34,8 +34,14 @@ struct bm_model_s {
     bool mma_current = false;
     alignas(64) unsigned char tmap_j[128] = {};
     alignas(64) unsigned char tmap_j1[128] = {};
+    // The same layout with bf16 hi/lo parts (split-precision fields), its
+    // 128-row one-slab tensor map, and its staleness flag.
+    void *Jt_bf = nullptr;
+    bool bf_current = false;
+    alignas(64) unsigned char tmap_bf1[128] = {};
     // Small device scratch for flags / reductions (owned).
-    int *dflags = nullptr;       // [8] check words; [3] = device error bits (1: wait timeout)
+    int *dflags = nullptr;       // [8] check words; [3] = device error bits (4: wait timeout);
+                                 // [4] = a scored sequence held a symbol >= q
     double *dred = nullptr;      // reduction partials, capacity red_cap doubles
     size_t red_cap = 0;
     int num_sms = 0;
@@ -143,6 +149,10 @@ int bm_launch_update(bm_model_s *m, const float *fi, const float *fij, const int
                      double *moments, cudaStream_t st);
 int bm_update_num_partials(int L);
 int bm_launch_energy(const float *h, const float *J, int L, int q, const uint8_t *seqs, int n,
-                     float *E, cudaStream_t st);
+                     float *E, int *bad, cudaStream_t st);
+int bm_split_prepare(bm_model_s *m, int bf16, cudaStream_t st);
+int bm_split_block_sites(int L, int q);
+int bm_launch_fields_simt(const bm_model_s *m, const uint8_t *seqs, int n, float *H, cudaStream_t st);
+int bm_launch_fields_tc(bm_model_s *m, const uint8_t *seqs, int n, float *H, int bf16, cudaStream_t st);
 int bm_launch_mutant_scan(const float *h, const float *J, int L, int q, const uint8_t *wt,
                           float *dE, cudaStream_t st);

@@ -62,6 +62,7 @@
 #include "bm_internal.cuh"
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -741,14 +742,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
     }
 }
 
-// Jt[nb*128 rows][Kp/64 slabs][2 (hi, lo)][64] fp16.  Row blk*128 + pp*q + a
-// holds site i = blk*B + pp, symbol a (pp < sites of the block; the other
-// rows of the 128 are zero); for column k = (j,b) of slab k/64,
-// hi = fp16(J_ij(a,b)) and lo = fp16(J_ij(a,b) - hi) (J_ij(a,b) = J[i][j][a][b]);
-// zero beyond L*q columns.  Each row interleaves the hi and lo slabs so one
-// 3-D TMA op brings both.
-__global__ void k_build_mma_layout(const float *__restrict__ J, __half *__restrict__ jt, int L, int q, int Kp, int B,
-                                   int nb)
+// Jt[nb*128 rows][Kp/64 slabs][2 (hi, lo)][64] of T (fp16 or bf16).  Row
+// blk*128 + pp*q + a holds site i = blk*B + pp, symbol a (pp < sites of the
+// block; the other rows of the 128 are zero); for column k = (j,b) of slab
+// k/64, hi = T(J_ij(a,b)) and lo = T(J_ij(a,b) - hi) (J_ij(a,b) = J[i][j][a][b],
+// round to nearest); zero beyond L*q columns.  Each row interleaves the hi and
+// lo slabs so one 3-D TMA op brings both.
+__device__ __forceinline__ __half to_t(float v, __half *) { return __float2half_rn(v); }
+__device__ __forceinline__ float from_t(__half v) { return __half2float(v); }
+__device__ __forceinline__ __nv_bfloat16 to_t(float v, __nv_bfloat16 *) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float from_t(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T>
+__global__ void k_build_mma_layout(const float *__restrict__ J, T *__restrict__ jt, int L, int q, int Kp, int B, int nb)
 {
     const size_t rows = (size_t)nb * kRowsA, n = rows * Kp;
     const int Q = L * q;
@@ -762,10 +768,10 @@ __global__ void k_build_mma_layout(const float *__restrict__ J, __half *__restri
             const int j = k / q, b = k % q;
             v = J[(((size_t)i * L + j) * q + a) * q + b];
         }
-        const __half vh = __float2half_rn(v);
+        const T vh = to_t(v, (T *)nullptr);
         const size_t o = r * (size_t)(2 * Kp) + (size_t)(k / kKC) * (2 * kKC) + (k % kKC);
         jt[o] = vh;
-        jt[o + kKC] = __float2half_rn(v - __half2float(vh));
+        jt[o + kKC] = to_t(v - from_t(vh), (T *)nullptr);
     }
 }
 
@@ -793,7 +799,8 @@ EncodeTiledFn encode_fn()
 // 128 bytes), 128B swizzle.  box_rows x box_slabs per op: {256, 2} lands
 // the hi tiles of two consecutive blocks and then their lo tiles; {128, 1}
 // one tile.
-int make_map(CUtensorMap *map, const __half *ptr, int rows, int Kp, int box_rows, int box_slabs)
+int make_map(CUtensorMap *map, const void *ptr, int rows, int Kp, int box_rows, int box_slabs,
+             CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return bm_fail(BM_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
@@ -801,7 +808,7 @@ int make_map(CUtensorMap *map, const __half *ptr, int rows, int Kp, int box_rows
     cuuint64_t strides[2] = {(cuuint64_t)Kp * 4, (cuuint64_t)kKC * 2};
     cuuint32_t box[3] = {(cuuint32_t)kKC, (cuuint32_t)box_rows, (cuuint32_t)box_slabs};
     cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<__half *>(ptr), dims, strides, box,
+    const CUresult r = fn(map, dt, 3, const_cast<void *>(ptr), dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return bm_fail(BM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -836,24 +843,38 @@ int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M)
     return nc >= 16 ? nc : 0;
 }
 
-int bm_mma_prepare(bm_model_s *m, cudaStream_t st)
+int bm_split_block_sites(int L, int q) { return block_sites(L, q); }
+
+// Bring the split layout of the live J up to date: fp16 (the sweep's, maps
+// tmap_j and tmap_j1) or bf16 (map tmap_bf1).
+int bm_split_prepare(bm_model_s *m, int bf16, cudaStream_t st)
 {
+    if (bf16 ? m->bf_current : m->mma_current) return BM_OK;
     const int B = block_sites(m->L, m->q), nb = (m->L + B - 1) / B;
     const int rows = nb * kRowsA;  // every block padded to 128 rows
     const int Kp = (m->L * m->q + kKC - 1) / kKC * kKC;
-    if (!m->Jt) {
+    void **buf = bf16 ? &m->Jt_bf : &m->Jt;
+    if (!*buf) {
         m->Kp = Kp;
-        BM_CK(cudaMalloc(&m->Jt, (size_t)rows * Kp * 2 * sizeof(__half)));
-        int rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_j), (const __half *)m->Jt, rows, Kp, 2 * kRowsA, 2);
-        if (rc == BM_OK)
-            rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_j1), (const __half *)m->Jt, rows, Kp, kRowsA, 1);
+        BM_CK(cudaMalloc(buf, (size_t)rows * Kp * 2 * sizeof(__half)));
+        int rc;
+        if (bf16) {
+            rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_bf1), *buf, rows, Kp, kRowsA, 1,
+                          CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+        } else {
+            rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_j), *buf, rows, Kp, 2 * kRowsA, 2);
+            if (rc == BM_OK) rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_j1), *buf, rows, Kp, kRowsA, 1);
+        }
         if (rc != BM_OK) return rc;
     }
     const size_t n = (size_t)rows * Kp;
     const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 64);
-    k_build_mma_layout<<<grid, 256, 0, st>>>(m->J, (__half *)m->Jt, m->L, m->q, Kp, B, nb);
+    if (bf16)
+        k_build_mma_layout<__nv_bfloat16><<<grid, 256, 0, st>>>(m->J, (__nv_bfloat16 *)*buf, m->L, m->q, Kp, B, nb);
+    else
+        k_build_mma_layout<__half><<<grid, 256, 0, st>>>(m->J, (__half *)*buf, m->L, m->q, Kp, B, nb);
     BM_CK_LAUNCH("k_build_mma_layout");
-    m->mma_current = true;
+    (bf16 ? m->bf_current : m->mma_current) = true;
     return BM_OK;
 }
 
@@ -861,8 +882,8 @@ int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, 
 {
     const int NC = bm_gibbs_mma_chains_per_cta(m, c->M);
     if (NC == 0) return bm_fail(BM_EINVAL, "tensor-core sweep: shape does not fit shared memory");
-    if (!m->mma_current) {
-        const int rc = bm_mma_prepare(m, st);
+    {
+        const int rc = bm_split_prepare(m, 0, st);
         if (rc != BM_OK) return rc;
     }
     MmaArgs a;

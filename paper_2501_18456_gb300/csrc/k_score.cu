@@ -44,7 +44,7 @@ __global__ void k_check_symbols(const uint8_t *__restrict__ s, size_t n, int q, 
 __global__ void __launch_bounds__(256) k_energy(const float *__restrict__ h,
                                                 const float *__restrict__ J, int L, int q,
                                                 const uint8_t *__restrict__ S, int n,
-                                                float *__restrict__ E)
+                                                float *__restrict__ E, int *bad)
 {
     extern __shared__ uint8_t sst[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -52,14 +52,22 @@ __global__ void __launch_bounds__(256) k_energy(const float *__restrict__ h,
     uint8_t *s = sst + (size_t)warp * L;
     const size_t qq = (size_t)q * q;
     for (long long k = (long long)blockIdx.x * nw + warp; k < n; k += (long long)gridDim.x * nw) {
-        for (int t = lane; t < L; t += 32) s[t] = S[(size_t)k * L + t];
+        bool inval = false;
+        for (int t = lane; t < L; t += 32) {
+            const uint8_t v = S[(size_t)k * L + t];
+            inval |= v >= q;
+            s[t] = v;
+        }
+        if (__any_sync(0xffffffffu, inval) && lane == 0) atomicOr(bad, 1);
         __syncwarp();
         float acc = 0.0f;
         for (int i = 0; i < L; ++i) {
             const int si = s[i];
+            if (si >= q) continue;  // a symbol >= q contributes nothing (flagged above)
             if (lane == 0) acc -= h[(size_t)i * q + si];
             const float *row = J + ((size_t)i * L) * qq + (size_t)si * q;
-            for (int j = i + 1 + lane; j < L; j += 32) acc -= __ldg(row + (size_t)j * qq + s[j]);
+            for (int j = i + 1 + lane; j < L; j += 32)
+                if (s[j] < q) acc -= __ldg(row + (size_t)j * qq + s[j]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -109,12 +117,12 @@ int bm_launch_check_symbols(const uint8_t *s, size_t n, int q, int *dflag, cudaS
 }
 
 int bm_launch_energy(const float *h, const float *J, int L, int q, const uint8_t *seqs, int n,
-                     float *E, cudaStream_t st)
+                     float *E, int *bad, cudaStream_t st)
 {
     if (n == 0) return BM_OK;
     const int warps = 8;
     const int grid = (int)std::min<long long>(((long long)n + warps - 1) / warps, 152LL * 16);
-    k_energy<<<grid, warps * 32, (size_t)warps * L, st>>>(h, J, L, q, seqs, n, E);
+    k_energy<<<grid, warps * 32, (size_t)warps * L, st>>>(h, J, L, q, seqs, n, E, bad);
     BM_CK_LAUNCH("k_energy");
     return BM_OK;
 }

@@ -24,6 +24,7 @@
 // chains' device error word (bit 2), every role leaves its loop and TMEM is
 // released.
 #include "bm_internal.cuh"
+#include "tc_common.cuh"
 
 #include <cuda.h>
 
@@ -31,6 +32,8 @@
 #include <mutex>
 
 namespace {
+
+using namespace bmtc;
 
 constexpr int kRows = 128;           // MMA M (rows (i,a) of a tile)
 constexpr int kCols = 256;           // MMA N (columns (j,b) of a tile)
@@ -40,94 +43,6 @@ constexpr int kStageA = kRows * kKB * kKS;  // 32 KB
 constexpr int kStageB = kCols * kKB * kKS;  // 64 KB
 constexpr int kNS = 2;               // stages
 constexpr int kThreads = 192;        // 6 warps
-constexpr uint64_t kWaitNs = 2000000000ull;
-
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
-{
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtimer() - t0 > kWaitNs) {
-            *abort_flag = 1;
-            atomicOr(err, 4);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
-// K-major 128B-swizzle matrix descriptor: start >> 4 [0,14), leading offset
-// (unused) [16,30), 8-row groups 1024 bytes apart [32,46), fixed 0b001 at
-// [46,49), layout 2 = 128B swizzle at [61,64).
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
-{
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
 
 // ---------------------------------------------------------------------------
 // X^T, E4M3 one-hot.  Block: 128 chains x 32 sites, 256 threads.
