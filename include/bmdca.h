@@ -298,6 +298,84 @@ enum {
  */
 int bm_fields(bm_model m, const uint8_t *seqs_dev, int n, float *H_dev, int form, void *stream);
 
+/*
+ * Serving with continuous batching (Sec. 4.1 sampling, Sec. 4.3 scoring,
+ * Sec. 4.4 single-mutant scans of trained models).
+ *
+ * A server keeps models resident and runs requests on a pool of CUDA
+ * streams from a worker thread.  Requests wait in arrival order; whenever a
+ * stream is free and the request's device scratch fits in the memory budget
+ * beside the requests already running, it is admitted (a later request that
+ * fits may start before an earlier one that does not), so work that arrives
+ * while other requests run joins them on the device as slots and memory
+ * free up.  Each request's result depends only on the request itself
+ * (sampling uses the request's own Philox key), so it is the same alone and
+ * in any mix.
+ *
+ * Host buffers (in / out) are owned by the caller and must stay valid until
+ * the request completes; pinned memory lets copies overlap other work
+ * (device pointers are accepted too).  Models must not be freed or have
+ * their parameters changed while the server holds them.  All bm_server_*
+ * calls are thread-safe.
+ */
+typedef struct bm_server_s *bm_server;
+
+enum {
+    BM_REQ_SAMPLE = 1,  /* n chains from uniform random states (Philox key `seed`, tag 1),
+                           nsweeps Gibbs sweeps at beta (draws keyed by `seed`, tag 0);
+                           out: uint8[n][L] final states.  Scratch n*L bytes. */
+    BM_REQ_SCORE = 2,   /* energies of n sequences, in: uint8[n][L]; out: float[n].
+                           Scratch n*(L+4) bytes. */
+    BM_REQ_SCAN = 3     /* single-mutant scan of the wild type in: uint8[L];
+                           out: float[L][q] (bm_mutant_scan).  Scratch L*(4q+1) bytes. */
+};
+
+typedef struct {
+    int type;         /* BM_REQ_* */
+    int model;        /* index returned by bm_server_add_model */
+    int n;            /* SAMPLE, SCORE: number of sequences (>= 1) */
+    int nsweeps;      /* SAMPLE: >= 0 */
+    float beta;       /* SAMPLE: finite */
+    uint64_t seed;    /* SAMPLE: Philox key of the request */
+    const void *in;   /* SCORE: uint8[n][L]; SCAN: uint8[L]; else unused */
+    void *out;        /* see BM_REQ_* */
+} bm_request;
+
+typedef struct {
+    long long submitted, completed, failed;
+    double p50_ms, p99_ms, mean_ms;  /* latency (submit to completion seen by the worker) */
+    double sequences;                /* SAMPLE n + SCORE n + SCAN L*q over completed requests */
+    double span_s;                   /* first submit to last completion */
+    int max_running;                 /* most requests on the device at once */
+} bm_server_stats;
+
+/* New server on the current device: `budget_bytes` of device scratch for
+ * running requests, `slots` streams (1..256).  BM_EINVAL / BM_ENOMEM. */
+int bm_server_create(size_t budget_bytes, int slots, bm_server *out);
+
+/* Drains (waits for every submitted request) and frees the server.  The
+ * models stay with the caller. */
+int bm_server_destroy(bm_server s);
+
+/* Makes a model resident; prepares its tensor-core layout (synchronously)
+ * so requests never rebuild it.  *id receives the model's index. */
+int bm_server_add_model(bm_server s, bm_model m, int *id);
+
+/* Queues a request (copied; the buffers are not).  *id receives its id.
+ * BM_EINVAL for a malformed request, BM_ENOMEM if its scratch alone
+ * exceeds the budget. */
+int bm_server_submit(bm_server s, const bm_request *r, uint64_t *id);
+
+/* Blocks until request `id` completes (timeout_ms < 0: no limit);
+ * *status receives its outcome (BM_OK or an error code), *latency_ms its
+ * latency.  BM_ETIMEOUT if it did not complete in time; BM_EINVAL for an
+ * unknown or already waited id. */
+int bm_server_wait(bm_server s, uint64_t id, double timeout_ms, int *status, double *latency_ms);
+
+/* Counters and latency percentiles of the requests completed so far;
+ * reset = 1 clears them afterwards. */
+int bm_server_stats_get(bm_server s, bm_server_stats *out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

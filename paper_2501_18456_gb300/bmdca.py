@@ -23,6 +23,21 @@ BM_HOST, BM_DEVICE = 0, 1
 BM_ENGINE_SIMT, BM_ENGINE_AUTO, BM_ENGINE_MMA = 0, 1, 2
 BM_STATS_AUTO, BM_STATS_SIMT, BM_STATS_MMA_BF16, BM_STATS_MMA_FP8 = 0, 1, 2, 3
 BM_FIELDS_FP32, BM_FIELDS_FP16X2, BM_FIELDS_BF16X2 = 0, 1, 2
+BM_REQ_SAMPLE, BM_REQ_SCORE, BM_REQ_SCAN = 1, 2, 3
+
+
+class Request(ctypes.Structure):
+    """bm_request (include/bmdca.h)."""
+    _fields_ = [("type", ctypes.c_int), ("model", ctypes.c_int), ("n", ctypes.c_int), ("nsweeps", ctypes.c_int),
+                ("beta", ctypes.c_float), ("seed", ctypes.c_uint64), ("in_", ctypes.c_void_p),
+                ("out", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    """bm_server_stats (include/bmdca.h)."""
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("sequences", ctypes.c_double), ("span_s", ctypes.c_double), ("max_running", ctypes.c_int)]
 
 # name -> (restype, argtypes); kept in the order of include/bmdca.h
 _P, _I, _U64, _F, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_float, ctypes.c_double
@@ -54,6 +69,12 @@ SIGNATURES = {
     "bm_energy_score": (_I, [_P, _P, _I, _P, _P]),
     "bm_mutant_scan": (_I, [_P, _P, _I, _P, _P]),
     "bm_fields": (_I, [_P, _P, _I, _P, _I, _P]),
+    "bm_server_create": (_I, [ctypes.c_size_t, _I, _P]),
+    "bm_server_destroy": (_I, [_P]),
+    "bm_server_add_model": (_I, [_P, _P, _P]),
+    "bm_server_submit": (_I, [_P, _P, _P]),
+    "bm_server_wait": (_I, [_P, _U64, _D, _P, _P]),
+    "bm_server_stats_get": (_I, [_P, _P, _I]),
 }
 
 
@@ -314,3 +335,62 @@ def bm_fields(m: Model, seqs: torch.Tensor, H: torch.Tensor, form: int = BM_FIEL
     ps = _dev(seqs, torch.uint8, n * m.L, "seqs")
     ph = _dev(H, torch.float32, n * m.L * m.q, "H")
     _check(lib().bm_fields(m.handle, ps, n, ph, form, _stream(stream)), "bm_fields")
+
+
+class Server:
+    """Owner of a bm_server handle (continuous-batching request server).
+
+    Keeps the models it serves (and the tensors of queued requests) alive
+    until the server is closed or the request is waited for."""
+
+    def __init__(self, budget_bytes: int, slots: int = 16):
+        h = ctypes.c_void_p()
+        _check(lib().bm_server_create(int(budget_bytes), int(slots), ctypes.byref(h)), "bm_server_create")
+        self.handle = h.value
+        self._models = []
+        self._pending = {}
+
+    def close(self):
+        if self.handle:
+            lib().bm_server_destroy(self.handle)
+            self.handle = None
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_model(self, m: Model) -> int:
+        i = ctypes.c_int()
+        _check(lib().bm_server_add_model(self.handle, m.handle, ctypes.byref(i)), "bm_server_add_model")
+        self._models.append(m)
+        return i.value
+
+    def submit(self, req_type: int, model: int, out: torch.Tensor, inp: torch.Tensor | None = None, n: int = 0,
+               nsweeps: int = 0, beta: float = 1.0, seed: int = 0) -> int:
+        """Queue a request; `out` (and `inp`) are contiguous host (pinned for overlap) or device tensors."""
+        for t in (out, inp):
+            if t is not None and not t.is_contiguous():
+                raise ValueError("request tensors must be contiguous")
+        r = Request(int(req_type), int(model), int(n), int(nsweeps), float(beta), int(seed),
+                    inp.data_ptr() if inp is not None else None, out.data_ptr())
+        rid = ctypes.c_uint64()
+        _check(lib().bm_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid)), "bm_server_submit")
+        self._pending[rid.value] = (out, inp)
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: float = -1.0):
+        """Block until request rid completes; returns (status, latency_ms)."""
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        _check(lib().bm_server_wait(self.handle, int(rid), float(timeout_ms), ctypes.byref(st), ctypes.byref(lat)),
+               "bm_server_wait")
+        self._pending.pop(rid, None)
+        return st.value, lat.value
+
+    def stats(self, reset: bool = False) -> dict:
+        out = ServerStats()
+        _check(lib().bm_server_stats_get(self.handle, ctypes.byref(out), 1 if reset else 0), "bm_server_stats_get")
+        return {k: getattr(out, k) for k, _ in ServerStats._fields_}

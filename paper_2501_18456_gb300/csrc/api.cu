@@ -327,7 +327,13 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
                        c->L, c->q, m->L, m->q);
     if (nsweeps < 0) return bm_fail(BM_EINVAL, "bm_gibbs_sweep: nsweeps=%d < 0", nsweeps);
     if (!isfinite(beta)) return bm_fail(BM_EINVAL, "bm_gibbs_sweep: beta not finite");
-    cudaStream_t st = (cudaStream_t)stream;
+    return bm_sweep_run(m, c, nsweeps, beta, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+int bm_sweep_run(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)
+{
     for (int done = 0; done < nsweeps;) {
         const int k = nsweeps - done < kMaxSweepsPerLaunch ? nsweeps - done : kMaxSweepsPerLaunch;
         // AUTO: the tensor-core sweep from q = 10 up (measured crossover between
@@ -342,6 +348,8 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
     }
     return BM_OK;
 }
+
+extern "C" {
 
 int bm_chain_stats(bm_chains c, int32_t *counts_dev, void *stream)
 {

@@ -133,6 +133,8 @@ int bm_gather_block_stride(int q);
 int bm_launch_build_gather(const float *J, float *Jg, int L, int q, cudaStream_t st);
 int bm_launch_gibbs_simt(const bm_model_s *m, bm_chains_s *c, int nsweeps, float beta,
                          cudaStream_t st);
+// nsweeps sweeps of the chains with the model's engine (no argument checks).
+int bm_sweep_run(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
 int bm_launch_chain_stats(const uint8_t *s, int M, int L, int q, int32_t *counts,
                           cudaStream_t st);
 int bm_launch_chain_stats_mma(const uint8_t *s, int M, int L, int q, int32_t *counts, int elem_bytes,
