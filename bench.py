@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-chains", type=int, default=0,
                     help="chains in the oracle sample (0: sized for ~15 s)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency leg")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -340,6 +342,26 @@ def run_ours(args, rank, world, local):
                        "note": "achieved = 2*M*(L(L+1)/2)*q^2 flops / CUDA-event time of bm_chain_stats "
                                "(one-hot build included); peak: fp8 = 2 x " + peak_src}
 
+    # ---- serving: Poisson stream of sample / score / mutant-scan requests over
+    # 32 resident models through the continuous-batching server (rank 0), with
+    # the tensor-core engine (default) and with plain FP32 sampling.
+    serve = None
+    if rank == 0 and not args.no_serve:
+        from paper_2501_18456_gb300 import serving
+        smodels = serving.make_models(32, 0)
+        tc = serving.run_stream(smodels, 10.0, args.serve_seconds, 1, engine=bmdca.BM_ENGINE_AUTO)
+        plain = serving.run_stream(smodels, 10.0, args.serve_seconds, 1, engine=bmdca.BM_ENGINE_SIMT)
+        serve = {"workload": "32 resident models (L U[60,400], q 21/5), Poisson 10 req/s: sample "
+                             "logU[1e2,1e4] seqs x U[20,200] sweeps at beta {0.8,1,1.2}, score "
+                             "logU[1e3,1e6] seqs, single-mutant scans",
+                 "p50_ms": tc["p50_ms"], "p99_ms": tc["p99_ms"], "mean_ms": tc["mean_ms"],
+                 "sequences_per_s": tc["sequences_per_s"], "requests": tc["requests"],
+                 "max_running": tc["max_running"],
+                 "plain_fp32": {k: plain[k] for k in ("p50_ms", "p99_ms", "mean_ms", "sequences_per_s",
+                                                      "requests", "max_running")}}
+        del smodels
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n = args.cpu_chains or calibrate_oracle_chains(15.0)
@@ -370,7 +392,7 @@ def run_ours(args, rank, world, local):
                 "e2e": {"value": world * site_updates_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps,
-                "clocks": clk, "rows_ms": rows, "wall_s_timed": t_wall}
+                "clocks": clk, "rows_ms": rows, "serve": serve, "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
