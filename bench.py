@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--cpu-chains", type=int, default=0,
                     help="chains in the oracle sample (0: sized for ~15 s)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-models leg")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
@@ -362,6 +363,14 @@ def run_ours(args, rank, world, local):
         del smodels
         torch.cuda.empty_cache()
 
+    # ---- batched: 64 models of uneven L swept in one graph launch (rank 0),
+    # against 64 sequential per-model launches.
+    batched = None
+    if rank == 0 and not args.no_batched:
+        from paper_2501_18456_gb300 import batched as batched_mod
+        batched = batched_mod.run(64, 2048, 10, 0)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n = args.cpu_chains or calibrate_oracle_chains(15.0)
@@ -392,7 +401,7 @@ def run_ours(args, rank, world, local):
                 "e2e": {"value": world * site_updates_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps,
-                "clocks": clk, "rows_ms": rows, "serve": serve, "wall_s_timed": t_wall}
+                "clocks": clk, "rows_ms": rows, "serve": serve, "batched": batched, "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

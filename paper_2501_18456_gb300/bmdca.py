@@ -69,6 +69,11 @@ SIGNATURES = {
     "bm_energy_score": (_I, [_P, _P, _I, _P, _P]),
     "bm_mutant_scan": (_I, [_P, _P, _I, _P, _P]),
     "bm_fields": (_I, [_P, _P, _I, _P, _I, _P]),
+    "bm_batch_create": (_I, [_P, _P, _I, _P]),
+    "bm_batch_free": (_I, [_P]),
+    "bm_batch_autotune": (_I, [_P, _P]),
+    "bm_batch_sweep": (_I, [_P, _I, _F, _P]),
+    "bm_batch_shape": (_I, [_P, _P, _P, _P]),
     "bm_server_create": (_I, [ctypes.c_size_t, _I, _P]),
     "bm_server_destroy": (_I, [_P]),
     "bm_server_add_model": (_I, [_P, _P, _P]),
@@ -394,3 +399,40 @@ class Server:
         out = ServerStats()
         _check(lib().bm_server_stats_get(self.handle, ctypes.byref(out), 1 if reset else 0), "bm_server_stats_get")
         return {k: getattr(out, k) for k, _ in ServerStats._fields_}
+
+
+class Batch:
+    """Owner of a bm_batch handle: CUDA-core sweeps of many (model, chains)
+    pairs with the same q in one graph launch.  Keeps the handles alive."""
+
+    def __init__(self, models, chains):
+        if len(models) != len(chains):
+            raise ValueError("one chains handle per model")
+        arr_m = (ctypes.c_void_p * len(models))(*[m.handle for m in models])
+        arr_c = (ctypes.c_void_p * len(chains))(*[c.handle for c in chains])
+        h = ctypes.c_void_p()
+        _check(lib().bm_batch_create(arr_m, arr_c, len(models), ctypes.byref(h)), "bm_batch_create")
+        self.handle = h.value
+        self._keep = (list(models), list(chains))
+
+    def close(self):
+        if self.handle:
+            lib().bm_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, stream=None):
+        _check(lib().bm_batch_autotune(self.handle, _stream(stream)), "bm_batch_autotune")
+
+    def sweep(self, nsweeps: int, beta: float = 1.0, stream=None):
+        _check(lib().bm_batch_sweep(self.handle, int(nsweeps), float(beta), _stream(stream)), "bm_batch_sweep")
+
+    def shape(self) -> dict:
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().bm_batch_shape(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "bm_batch_shape")
+        return {"chains_per_cta": a.value, "stages": b.value, "ctas": c.value}

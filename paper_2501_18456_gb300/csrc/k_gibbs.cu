@@ -28,6 +28,8 @@
 #include "bm_internal.cuh"
 
 #include <algorithm>
+#include <new>
+#include <vector>
 
 namespace {
 
@@ -168,6 +170,14 @@ struct GibbsArgs {
     int M, L, q, Lp, bs, jc, nch, ns, cpc, nsweeps;
 };
 
+// One CTA of a batched launch: the model and chains it works on (h, Jg,
+// states, err, seed, sweep0, M, L, Lp, nch differ per model; the rest is
+// the launch's common shape) and the index of its first chain.
+struct BatchItem {
+    GibbsArgs a;
+    long long chain0;
+};
+
 // Shared memory: [ns stages of jc*bs floats][cpc x Lp u32 row offsets]
 // [2*ns mbarriers][abort flag].  The row offset of chain c at site j is
 // the byte offset, inside a stage, of row (j mod jc, s_j):
@@ -180,10 +190,13 @@ struct GibbsArgs {
 // JCC: compile-time chunk length for fully unrolled full chunks (0: use the
 // runtime loop for every chunk).  blockDim = (consumer warps + 1) * 32; the
 // last warp is the producer.
-template <int GW, int R, int JCC>
-__global__ void __launch_bounds__(1024, 1) k_gibbs_staged(const GibbsArgs p)
+template <int GW, int R, int JCC, bool BATCH>
+__global__ void __launch_bounds__(1024, 1) k_gibbs_staged(const GibbsArgs p0, const BatchItem *__restrict__ items)
 {
     constexpr int G = 32 / GW;
+    // batched launch: this CTA's model and first chain come from the work list
+    const GibbsArgs p = BATCH ? items[blockIdx.x].a : p0;
+    const size_t cta0 = BATCH ? (size_t)items[blockIdx.x].chain0 : (size_t)blockIdx.x * p0.cpc;
     extern __shared__ __align__(128) unsigned char smem[];
     const int nwc = (blockDim.x >> 5) - 1;  // consumer warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -202,7 +215,6 @@ __global__ void __launch_bounds__(1024, 1) k_gibbs_staged(const GibbsArgs p)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const size_t cta0 = (size_t)blockIdx.x * p.cpc;
     for (int k = threadIdx.x; k < p.cpc * p.Lp; k += blockDim.x) {
         const int c = k / p.Lp, x = k - c * p.Lp;
         const size_t m = cta0 + c;
@@ -363,24 +375,50 @@ Shape pick_shape(const bm_model_s *m, int M)
     return s;
 }
 
+// attr_only: set the kernel's shared-memory limit and launch nothing (done
+// before a stream capture).
 template <int GW, int R, int JCC>
-int launch_staged(const GibbsArgs &a, const Shape &s, cudaStream_t st)
+int launch_staged(const GibbsArgs &a, const Shape &s, cudaStream_t st, const BatchItem *items = nullptr,
+                  bool attr_only = false)
 {
-    auto kern = k_gibbs_staged<GW, R, JCC>;
-    BM_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem));
-    kern<<<s.grid, (s.warps + 1) * 32, s.smem, st>>>(a);
+    if (items) {
+        auto kern = k_gibbs_staged<GW, R, JCC, true>;
+        if (attr_only) {
+            BM_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem));
+            return BM_OK;
+        }
+        kern<<<s.grid, (s.warps + 1) * 32, s.smem, st>>>(a, items);
+    } else {
+        auto kern = k_gibbs_staged<GW, R, JCC, false>;
+        BM_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem));
+        kern<<<s.grid, (s.warps + 1) * 32, s.smem, st>>>(a, nullptr);
+    }
     BM_CK_LAUNCH("k_gibbs_staged");
     return BM_OK;
 }
 
 template <int GW, int JCC>
-int dispatch_r(const GibbsArgs &a, const Shape &s, cudaStream_t st)
+int dispatch_r(const GibbsArgs &a, const Shape &s, cudaStream_t st, const BatchItem *items = nullptr,
+               bool attr_only = false)
 {
     switch (s.R) {
-    case 1: return launch_staged<GW, 1, JCC>(a, s, st);
-    case 2: return launch_staged<GW, 2, JCC>(a, s, st);
-    case 3: return launch_staged<GW, 3, JCC>(a, s, st);
-    default: return launch_staged<GW, 4, JCC>(a, s, st);
+    case 1: return launch_staged<GW, 1, JCC>(a, s, st, items, attr_only);
+    case 2: return launch_staged<GW, 2, JCC>(a, s, st, items, attr_only);
+    case 3: return launch_staged<GW, 3, JCC>(a, s, st, items, attr_only);
+    default: return launch_staged<GW, 4, JCC>(a, s, st, items, attr_only);
+    }
+}
+
+int dispatch_shape(const GibbsArgs &a, const Shape &s, cudaStream_t st, const BatchItem *items,
+                   bool attr_only = false)
+{
+    if (s.jcc == 16) return dispatch_r<32, 16>(a, s, st, items, attr_only);
+    if (s.jcc == 64) return dispatch_r<8, 64>(a, s, st, items, attr_only);
+    switch (s.GW) {
+    case 4: return dispatch_r<4, 0>(a, s, st, items, attr_only);
+    case 8: return dispatch_r<8, 0>(a, s, st, items, attr_only);
+    case 16: return dispatch_r<16, 0>(a, s, st, items, attr_only);
+    default: return dispatch_r<32, 0>(a, s, st, items, attr_only);
     }
 }
 
@@ -428,12 +466,312 @@ int bm_launch_gibbs_simt(const bm_model_s *m, bm_chains_s *c, int nsweeps, float
     a.ns = s.ns;
     a.cpc = s.cpc;
     a.nsweeps = nsweeps;
-    if (s.jcc == 16) return dispatch_r<32, 16>(a, s, st);
-    if (s.jcc == 64) return dispatch_r<8, 64>(a, s, st);
-    switch (s.GW) {
-    case 4: return dispatch_r<4, 0>(a, s, st);
-    case 8: return dispatch_r<8, 0>(a, s, st);
-    case 16: return dispatch_r<16, 0>(a, s, st);
-    default: return dispatch_r<32, 0>(a, s, st);
+    return dispatch_shape(a, s, st, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Batched sweeps of many independent models (same q) in one launch.
+//
+// The work list holds one entry per CTA: a tile of cpc chains of one model.
+// Entries are ordered by decreasing cost (L^2 per chain: the longest models
+// first, so the tail of the launch is filled with short tiles).  All entries
+// share the launch shape (warp layout, stages, chains per CTA, chunk
+// length); shared memory is sized for the longest model.  The list lives in
+// device memory and is refreshed from a pinned host copy by the first node
+// of a captured CUDA graph, so each call is one graph launch that picks up
+// the models' current parameter pointers and sweep counters.
+// ---------------------------------------------------------------------------
+namespace {
+
+bool batch_shape(int q, int bs, int Lmax, int cpc_target, int ns, int nsm, Shape *out)
+{
+    Shape s{};
+    s.GW = q <= 4 ? 4 : q <= 8 ? 8 : q <= 16 ? 16 : 32;
+    const int G = 32 / s.GW;
+    const size_t row = (size_t)bs * 4;
+    int jc = (int)(kStageTarget / row);
+    s.jc = std::max(4, std::min(64, jc & ~3));
+    const size_t stage = (size_t)s.jc * row;
+    const int Lp = (Lmax + 15) & ~15;
+    int R = (cpc_target + 31 * G - 1) / (31 * G);
+    R = std::max(1, std::min(4, R));
+    int warps = (cpc_target + G * R - 1) / (G * R);
+    warps = std::max(1, std::min(31, warps));
+    s.R = R;
+    s.warps = warps;
+    s.cpc = warps * G * R;
+    s.ns = ns;
+    s.smem = (size_t)ns * stage + (size_t)s.cpc * Lp * 4 + 2 * ns * 8 + 16;
+    s.jcc = (s.GW == 32 && s.jc == 16) ? 16 : (s.GW == 8 && s.jc == 64) ? 64 : 0;
+    (void)nsm;
+    *out = s;
+    return s.smem <= kSmemBudget;
+}
+
+}  // namespace
+
+struct bm_batch_s {
+    std::vector<bm_model_s *> models;
+    std::vector<bm_chains_s *> chains;
+    int q = 0, bs = 0, Lmax = 0, nsm = 1;
+    Shape shape{};
+    bool tuned = false;
+    int nitems = 0;
+    BatchItem *items_dev = nullptr;
+    BatchItem *items_host[2] = {nullptr, nullptr};  // pinned, alternating
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaEvent_t used[2] = {nullptr, nullptr};        // last launch that read items_host[k]
+    int next = 0;
+    std::vector<int> order;                          // model index of each tile, LPT order
+    std::vector<long long> first;                    // first chain of each tile
+};
+
+namespace {
+
+// Tiles of the batch for chains-per-CTA cpc, longest models first.
+void build_tiles(bm_batch_s *b, int cpc)
+{
+    std::vector<int> idx(b->models.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = (int)k;
+    std::stable_sort(idx.begin(), idx.end(), [b](int x, int y) { return b->models[x]->L > b->models[y]->L; });
+    b->order.clear();
+    b->first.clear();
+    for (int k : idx)
+        for (long long c0 = 0; c0 < b->chains[k]->M; c0 += cpc) {
+            b->order.push_back(k);
+            b->first.push_back(c0);
+        }
+    b->nitems = (int)b->order.size();
+}
+
+void fill_items(const bm_batch_s *b, BatchItem *dst, int nsweeps, float beta, uint8_t *const *states_override)
+{
+    const Shape &s = b->shape;
+    for (int t = 0; t < b->nitems; ++t) {
+        const int k = b->order[t];
+        const bm_model_s *m = b->models[k];
+        const bm_chains_s *c = b->chains[k];
+        GibbsArgs &a = dst[t].a;
+        a.h = m->h;
+        a.Jg = m->Jg;
+        a.states = states_override ? states_override[k] : c->s;
+        a.err = m->dflags + 3;
+        a.seed = c->seed;
+        a.sweep0 = c->sweep;
+        a.beta = beta;
+        a.M = c->M;
+        a.L = c->L;
+        a.q = c->q;
+        a.Lp = (c->L + 15) & ~15;
+        a.bs = m->bs;
+        a.jc = s.jc;
+        a.nch = (c->L + s.jc - 1) / s.jc;
+        a.ns = s.ns;
+        a.cpc = s.cpc;
+        a.nsweeps = nsweeps;
+        dst[t].chain0 = b->first[t];
     }
 }
+
+void drop_graphs(bm_batch_s *b)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (b->used[k]) cudaEventSynchronize(b->used[k]);
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+        b->graph[k] = nullptr;
+        cudaFreeHost(b->items_host[k]);
+        b->items_host[k] = nullptr;
+    }
+    cudaFree(b->items_dev);
+    b->items_dev = nullptr;
+}
+
+// (Re)build the work list, its buffers and the two graphs for the current shape.
+int prepare(bm_batch_s *b, cudaStream_t st)
+{
+    drop_graphs(b);
+    build_tiles(b, b->shape.cpc);
+    b->shape.grid = b->nitems;
+    const size_t bytes = (size_t)b->nitems * sizeof(BatchItem);
+    BM_CK(cudaMalloc(&b->items_dev, bytes));
+    for (int k = 0; k < 2; ++k) {
+        BM_CK(cudaMallocHost(&b->items_host[k], bytes));
+        fill_items(b, b->items_host[k], 0, 1.0f, nullptr);
+        if (!b->used[k]) BM_CK(cudaEventCreateWithFlags(&b->used[k], cudaEventDisableTiming));
+    }
+    {
+        GibbsArgs dummy{};
+        const int rc0 = dispatch_shape(dummy, b->shape, nullptr, b->items_dev, true);
+        if (rc0 != BM_OK) return rc0;
+    }
+    cudaStream_t cap;
+    BM_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = BM_OK;
+    for (int k = 0; k < 2 && rc == BM_OK; ++k) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            e = cudaMemcpyAsync(b->items_dev, b->items_host[k], bytes, cudaMemcpyHostToDevice, cap);
+            if (e == cudaSuccess) {
+                GibbsArgs dummy{};
+                rc = dispatch_shape(dummy, b->shape, cap, b->items_dev);
+            }
+            const cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess && rc == BM_OK) e = cudaGraphInstantiate(&b->graph[k], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess && rc == BM_OK) rc = bm_cuda_fail(e, "bm_batch: graph capture");
+    }
+    cudaStreamDestroy(cap);
+    (void)st;
+    return rc;
+}
+
+int launch_graph(bm_batch_s *b, int nsweeps, float beta, cudaStream_t st, uint8_t *const *states_override)
+{
+    const int k = b->next;
+    b->next ^= 1;
+    BM_CK(cudaEventSynchronize(b->used[k]));  // the previous launch that read this host copy has run
+    fill_items(b, b->items_host[k], nsweeps, beta, states_override);
+    BM_CK(cudaGraphLaunch(b->graph[k], st));
+    BM_CK(cudaEventRecord(b->used[k], st));
+    return BM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bm_batch_create(const bm_model *models, const bm_chains *chains, int count, bm_batch *out)
+{
+    if (!out) return bm_fail(BM_EINVAL, "bm_batch_create: out is NULL");
+    *out = nullptr;
+    if (!models || !chains || count < 1) return bm_fail(BM_EINVAL, "bm_batch_create: empty batch");
+    bm_batch_s *b = new (std::nothrow) bm_batch_s();
+    if (!b) return bm_fail(BM_ENOMEM, "bm_batch_create: host allocation failed");
+    for (int k = 0; k < count; ++k) {
+        bm_model_s *m = models[k];
+        bm_chains_s *c = chains[k];
+        int rc = BM_OK;
+        if (!m || !c) rc = bm_fail(BM_EINVAL, "bm_batch_create: NULL handle at %d", k);
+        else if (c->L != m->L || c->q != m->q) rc = bm_fail(BM_EINVAL, "bm_batch_create: chains %d do not match model", k);
+        else if (k > 0 && m->q != b->q) rc = bm_fail(BM_EINVAL, "bm_batch_create: all models need the same q");
+        if (rc != BM_OK) {
+            delete b;
+            return rc;
+        }
+        b->models.push_back(m);
+        b->chains.push_back(c);
+        b->q = m->q;
+        b->bs = m->bs;
+        b->Lmax = std::max(b->Lmax, m->L);
+        b->nsm = m->num_sms > 0 ? m->num_sms : 1;
+    }
+    // default shape: the largest chains-per-CTA that fits with 3 stages
+    int rc = bm_fail(BM_EINVAL, "bm_batch_create: L=%d does not fit shared memory", b->Lmax);
+    for (int cpc : {124, 96, 64, 48, 32, 16, 8}) {
+        for (int ns : {3, 2}) {
+            Shape s;
+            if (batch_shape(b->q, b->bs, b->Lmax, cpc, ns, b->nsm, &s)) {
+                b->shape = s;
+                rc = BM_OK;
+                break;
+            }
+        }
+        if (rc == BM_OK) break;
+    }
+    if (rc == BM_OK) rc = prepare(b, nullptr);
+    if (rc != BM_OK) {
+        drop_graphs(b);
+        for (auto &e : b->used)
+            if (e) cudaEventDestroy(e);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return BM_OK;
+}
+
+int bm_batch_free(bm_batch b)
+{
+    if (!b) return BM_OK;
+    drop_graphs(b);
+    for (auto &e : b->used)
+        if (e) cudaEventDestroy(e);
+    delete b;
+    return BM_OK;
+}
+
+int bm_batch_sweep(bm_batch b, int nsweeps, float beta, void *stream)
+{
+    if (!b) return bm_fail(BM_EINVAL, "bm_batch_sweep: NULL batch");
+    if (nsweeps < 0) return bm_fail(BM_EINVAL, "bm_batch_sweep: nsweeps=%d < 0", nsweeps);
+    if (!isfinite(beta)) return bm_fail(BM_EINVAL, "bm_batch_sweep: beta not finite");
+    if (nsweeps == 0) return BM_OK;
+    const int rc = launch_graph(b, nsweeps, beta, (cudaStream_t)stream, nullptr);
+    if (rc != BM_OK) return rc;
+    for (auto *c : b->chains) c->sweep += (uint64_t)nsweeps;
+    return BM_OK;
+}
+
+int bm_batch_autotune(bm_batch b, void *stream)
+{
+    if (!b) return bm_fail(BM_EINVAL, "bm_batch_autotune: NULL batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    // scratch copies of the states: tuning sweeps must not move the chains
+    std::vector<uint8_t *> scratch(b->chains.size(), nullptr);
+    int rc = BM_OK;
+    for (size_t k = 0; k < b->chains.size() && rc == BM_OK; ++k) {
+        const size_t n = (size_t)b->chains[k]->M * b->chains[k]->L;
+        cudaError_t e = cudaMalloc(&scratch[k], n);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(scratch[k], b->chains[k]->s, n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) rc = bm_cuda_fail(e, "bm_batch_autotune: scratch");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == BM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = bm_fail(BM_ECUDA, "bm_batch_autotune: events");
+    Shape best = b->shape;
+    float best_ms = 1e30f;
+    for (int cpc : {16, 32, 48, 64, 96, 124}) {
+        for (int ns : {2, 3, 4}) {
+            if (rc != BM_OK) break;
+            Shape s;
+            if (!batch_shape(b->q, b->bs, b->Lmax, cpc, ns, b->nsm, &s)) continue;
+            b->shape = s;
+            rc = prepare(b, st);
+            if (rc != BM_OK) break;
+            rc = launch_graph(b, 1, 1.0f, st, scratch.data());  // warm-up
+            if (rc == BM_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = bm_fail(BM_ECUDA, "autotune event");
+            for (int r = 0; r < 2 && rc == BM_OK; ++r) rc = launch_graph(b, 1, 1.0f, st, scratch.data());
+            if (rc == BM_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = bm_fail(BM_ECUDA, "autotune event");
+            float ms = 0.0f;
+            if (rc == BM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = bm_fail(BM_ECUDA, "autotune timing");
+            if (rc == BM_OK && ms < best_ms) {
+                best_ms = ms;
+                best = s;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    for (auto *p : scratch) cudaFree(p);
+    b->shape = best;
+    const int rc2 = prepare(b, st);
+    if (rc == BM_OK) rc = rc2;
+    b->tuned = rc == BM_OK;
+    return rc;
+}
+
+int bm_batch_shape(bm_batch b, int *chains_per_cta, int *stages, int *ctas)
+{
+    if (!b) return bm_fail(BM_EINVAL, "bm_batch_shape: NULL batch");
+    if (chains_per_cta) *chains_per_cta = b->shape.cpc;
+    if (stages) *stages = b->shape.ns;
+    if (ctas) *ctas = b->nitems;
+    return BM_OK;
+}
+
+}  // extern "C"
