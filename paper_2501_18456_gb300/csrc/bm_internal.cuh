@@ -56,11 +56,10 @@ struct bm_chains_s {
     int stats_engine = BM_STATS_AUTO;
     int *derr = nullptr;   // device error word of this handle's kernels
     // Transposed FP8 one-hot of the states for the tensor-core counts
-    // (xt_rows x xt_cols bytes, owned) and its two TMA tensor maps.
+    // (xt_rows x xt_cols bytes, owned) and its TMA tensor map.
     void *xt = nullptr;
     int xt_rows = 0, xt_cols = 0;
     alignas(64) unsigned char tmap_a[128] = {};
-    alignas(64) unsigned char tmap_b[128] = {};
 };
 
 // ---------------------------------------------------------------------------

@@ -199,6 +199,20 @@ __device__ __forceinline__ void named_bar(int id, int n)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// Named barrier returning the OR of `pred` over its n threads (the same
+// answer in every participant).
+__device__ __forceinline__ bool named_bar_or(int id, int n, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
 // Byte offset of 16-byte piece p of row r in a no-swizzle K-major tile with
 // 8 pieces per row: core matrix (r/8, p) at ((r/8)*8 + p)*128, row r%8 at +16*(r%8).
 __device__ __forceinline__ uint32_t noswz_off(int r, int p)
@@ -551,8 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int k = w; k < g.Bk * q; k += 128) hrow[k] = p.h[(size_t)g.i0 * q + k];
             if (ok && !mbar_wait(corr_bar, (uint32_t)(kb & 1), abort_flag, p.err)) ok = false;
-            named_bar(1, 128);
-            if (*abort_flag) ok = false;  // uniform from here on
+            ok = !named_bar_or(1, 128, !ok || *abort_flag);  // one decision for every drawer
             // --- sequential redraw of block kb, one site at a time, one thread per chain
             const uint8_t *old = snap_of(kb);
             const uint32_t tacc = tmem + ((uint32_t)lane_base << 16) + (uint32_t)slot * p.acc_stride;

@@ -11,15 +11,15 @@
 //                chain columns, zero padded to a multiple of 256), coalesced
 //                16-byte stores from a shared-memory transpose of the states;
 //   k_counts_tc  persistent over the output tiles that hold some pair i <= j.
-//                A tile is 128 rows (i,a) = TI = floor(128/q) sites by 256
-//                columns (j,b) = TJ = floor(256/q) sites.  warp 0 streams the
-//                A (128 rows) and B (256 rows) operand tiles of 256 chains per
-//                stage by TMA (3-D views, 128B swizzle) into a 2-stage ring;
-//                warp 1 issues 8 MMAs per stage (kind::f8f6f4, M = 128,
-//                N = 256, K = 32) into one of two TMEM accumulators; warps 2-5
-//                read the finished accumulator (one TMEM lane = one row) and
-//                store the int32 counts of the blocks i <= j in the upper
-//                block-triangle layout while the next tile accumulates.
+//                A tile is 256 rows (i,a) x 256 columns (j,b), T = floor(256/q)
+//                sites each way.  warp 0 streams the A (256 rows) and B (256
+//                rows) operand tiles of 128 chains per stage by TMA (3-D
+//                view, 128B swizzle) into a 3-stage ring; warp 1 issues 8 MMAs
+//                per stage (kind::f8f6f4, M = 128, N = 256, K = 32: each B
+//                tile feeds the two 128-row halves of A) into two TMEM
+//                accumulators (512 columns); warps 2-9 read them (one TMEM
+//                lane = one row) and store the int32 counts of the blocks
+//                i <= j in the upper block-triangle layout.
 // Every mbarrier wait is bounded by %globaltimer (2 s); a timeout sets the
 // chains' device error word (bit 2), every role leaves its loop and TMEM is
 // released.
@@ -35,14 +35,15 @@ namespace {
 
 using namespace bmtc;
 
-constexpr int kRows = 128;           // MMA M (rows (i,a) of a tile)
-constexpr int kCols = 256;           // MMA N (columns (j,b) of a tile)
-constexpr int kKB = 128;             // chains (bytes) per swizzle atom row
-constexpr int kKS = 2;               // atoms per stage: 256 chains
-constexpr int kStageA = kRows * kKB * kKS;  // 32 KB
-constexpr int kStageB = kCols * kKB * kKS;  // 64 KB
-constexpr int kNS = 2;               // stages
-constexpr int kThreads = 192;        // 6 warps
+constexpr int kTile = 256;           // output tile: 256 rows (i,a) x 256 columns (j,b)
+constexpr int kHalf = 128;           // MMA M: one accumulator per 128-row half of the tile
+constexpr int kKB = 128;             // chains per stage (one 128-byte swizzle atom per row)
+constexpr int kKS = 1;               // atoms per stage
+constexpr int kStageA = kTile * kKB; // 32 KB
+constexpr int kStageB = kTile * kKB; // 32 KB
+constexpr int kNS = 3;               // stages
+constexpr int kThreads = 320;        // 10 warps: producer, MMA issuer, 8 epilogue warps
+constexpr int kStgStride = 33;       // staging row stride (floats): conflict-free both ways
 
 // ---------------------------------------------------------------------------
 // X^T, E4M3 one-hot.  Block: 128 chains x 32 sites, 256 threads.
@@ -109,19 +110,20 @@ __device__ __forceinline__ void tile_of(const CtArgs &p, int t, int &ti, int &tj
     tj = 0;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_counts_tc(const __grid_constant__ CUtensorMap tm_a,
-                                                           const __grid_constant__ CUtensorMap tm_b, const CtArgs p)
+__global__ void __launch_bounds__(kThreads, 1) k_counts_tc(const __grid_constant__ CUtensorMap tm_x, const CtArgs p)
 {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = su32(smem_raw);
     unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    // stage s: A at s*(kStageA + kStageB), B right after
-    uint64_t *bars = reinterpret_cast<uint64_t *>(base + kNS * (kStageA + kStageB));
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kNS + 5);
+    // stage s: A (256 rows) at s*(kStageA + kStageB), B (256 rows) right after;
+    // then the epilogue's staging of one 32-column slab of the tile
+    float *stg = reinterpret_cast<float *>(base + kNS * (kStageA + kStageB));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stg + kTile * kStgStride);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kNS + 3);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const uint32_t full = su32(bars), empty = full + 8 * kNS;
-    const uint32_t acc_full = empty + 8 * kNS, acc_empty = acc_full + 16;
-    const uint32_t fin = acc_empty + 16;  // completion of every MMA issued (teardown)
+    const uint32_t acc_full = empty + 8 * kNS, acc_empty = acc_full + 8;
+    const uint32_t fin = acc_empty + 8;  // completion of every MMA issued (teardown)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = p.q, L = p.L;
 
@@ -130,17 +132,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts_tc(const __grid_constant
             mbar_init(full + 8 * s, 1);
             mbar_init(empty + 8 * s, 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(acc_full + 8 * b, 1);
-            mbar_init(acc_empty + 8 * b, 4);
-        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 8);
         mbar_init(fin, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(2 * kCols)
+                     "r"(2 * kTile)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -165,8 +165,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts_tc(const __grid_constant
                     }
                     const uint32_t dst = su32(base + s * (kStageA + kStageB));
                     mbar_expect_tx(full + 8 * s, kStageA + kStageB);
-                    tma_load_3d(dst, &tm_a, 0, ti * p.TI * q, k * kKS, full + 8 * s);
-                    tma_load_3d(dst + kStageA, &tm_b, 0, tj * p.TJ * q, k * kKS, full + 8 * s);
+                    tma_load_3d(dst, &tm_x, 0, ti * p.TI * q, k, full + 8 * s);
+                    tma_load_3d(dst + kStageA, &tm_x, 0, tj * p.TJ * q, k, full + 8 * s);
                     ++issued;
                     if (++s == kNS) {
                         s = 0;
@@ -184,19 +184,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts_tc(const __grid_constant
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             // kind::f8f6f4: D F32 (bit 4), A = B = E4M3 (0), K-major, N >> 3 at 17, M >> 4 at 24.
-            const uint32_t idesc = (1u << 4) | ((uint32_t)(kCols >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kHalf >> 4) << 24);
             int s = 0;
             uint32_t ph = 0;
             int n = 0;  // tiles done by this CTA
             bool ok = true;
             for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++n) {
-                const int buf = n & 1;
-                if (n >= 2 && !mbar_wait(acc_empty + 8 * buf, (uint32_t)(((n - 2) >> 1) & 1), abort_flag, p.err)) {
+                if (n >= 1 && !mbar_wait(acc_empty, (uint32_t)((n - 1) & 1), abort_flag, p.err)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t dcol = tmem + (uint32_t)buf * kCols;
                 for (int k = 0; k < p.nstages; ++k) {
                     if (!mbar_wait(full + 8 * s, ph, abort_flag, p.err)) {
                         ok = false;
@@ -205,11 +203,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts_tc(const __grid_constant
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = su32(base + s * (kStageA + kStageB)), b0 = a0 + kStageA;
 #pragma unroll
-                    for (int u = 0; u < kKS; ++u)
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            mma_f8(dcol, desc_sw128(a0 + u * kRows * kKB + kk * 32),
-                                   desc_sw128(b0 + u * kCols * kKB + kk * 32), idesc, (k > 0 || u > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t bd = desc_sw128(b0 + kk * 32);
+                        const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+                        mma_f8(tmem, desc_sw128(a0 + kk * 32), bd, idesc, acc);                       // rows 0-127
+                        mma_f8(tmem + kTile, desc_sw128(a0 + kHalf * kKB + kk * 32), bd, idesc, acc);  // rows 128-255
+                    }
                     mma_commit(empty + 8 * s);
                     if (++s == kNS) {
                         s = 0;
@@ -217,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts_tc(const __grid_constant
                     }
                 }
                 if (!ok) break;
-                mma_commit(acc_full + 8 * buf);
+                mma_commit(acc_full);
             }
             // all MMAs of this thread retired before TMEM is released (also after an abort)
             mma_commit(fin);
@@ -225,46 +224,51 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts_tc(const __grid_constant
             mbar_wait(fin, 0, &no_abort, p.err);
         }
     } else {
-        // ------------------------------------------------------------ epilogue (warps 2-5)
+        // ------------------------------------------------------------ epilogue (warps 2-9)
+        // Per 32-column slab: each warp copies its 32 accumulator rows to the
+        // staging buffer (one row per lane), then the 256 threads write the
+        // slab out row by row, 32 consecutive columns per warp, so a store
+        // covers a contiguous run of a block row.  Uniform control flow (the
+        // named barriers) also after an abort.
+        const int half = (warp - 2) >> 2;  // accumulator: tile rows [128*half, 128*half + 128)
         const int lane_base = 32 * (warp & 3);
-        const int r = lane_base + lane;  // TMEM lane = tile row
-        const int il = r / q, a = r - il * q;
+        const int r = half * kHalf + lane_base + lane;  // tile row copied by this thread
+        const int e = tid - 64;                          // 0..255
         int n = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++n) {
             int ti, tj;
             tile_of(p, t, ti, tj);
-            const int buf = n & 1;
-            if (ok && !mbar_wait(acc_full + 8 * buf, (uint32_t)((n >> 1) & 1), abort_flag, p.err)) ok = false;
-            if (!ok) break;
+            if (ok && !mbar_wait(acc_full, (uint32_t)(n & 1), abort_flag, p.err)) ok = false;
+            if (named_bar_or(1, 256, !ok || *abort_flag)) {  // the same decision in every epilogue thread
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int i = ti * p.TI + il;
-            const bool row_ok = il < p.TI && i < L;
-            for (int c0 = 0; c0 < kCols; c0 += 32) {
+            for (int c0 = 0; c0 < kTile; c0 += 32) {
                 uint32_t v[32];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(tmem + ((uint32_t)lane_base << 16) + (uint32_t)buf * kCols + (uint32_t)c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (!row_ok) continue;
+                tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)half * kTile + (uint32_t)c0, v);
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const int cc = c0 + e;
-                    const int jl = cc / q, b = cc - jl * q;
-                    const int j = tj * p.TJ + jl;
-                    if (jl < p.TJ && j < L && j >= i)
-                        p.counts[bm_pair_block(L, i, j) * q * q + (size_t)a * q + b] = (int32_t)__uint_as_float(v[e]);
+                for (int x = 0; x < 32; ++x) stg[r * kStgStride + x] = __uint_as_float(v[x]);
+                named_bar_sync(1, 256);
+                // write-out: thread e handles column c0 + (e & 31) of rows e/32, e/32 + 8, ...
+                const int cc = c0 + (e & 31);
+                const int jl = cc / q, b = cc - jl * q;
+                const int j = tj * p.TJ + jl;
+                if (jl < p.TJ && j < L) {
+                    for (int rr = e >> 5; rr < kTile; rr += 8) {
+                        const int il = rr / q, a = rr - il * q;
+                        const int i = ti * p.TI + il;
+                        if (il < p.TI && i <= j)
+                            p.counts[bm_pair_block(L, i, j) * q * q + (size_t)a * q + b] =
+                                (int32_t)stg[rr * kStgStride + (e & 31)];
+                    }
                 }
+                named_bar_sync(1, 256);  // staging is rewritten by the next slab
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty + 8 * buf);
+            if (lane == 0) mbar_arrive(acc_empty);
         }
         if (!ok) *abort_flag = 1;
     }
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts_tc(const __grid_constant
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTile) : "memory");
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -319,7 +323,7 @@ int bm_launch_chain_stats_tc(bm_chains_s *c, int32_t *counts, cudaStream_t st)
     const int M = c->M, L = c->L, q = c->q;
     if (M >= (1 << 24)) return bm_fail(BM_EINVAL, "chain_stats (tensor cores): M >= 2^24 not exact in FP32");
     const int Q = L * q;
-    const int Mp = (M + kKB * kKS - 1) / (kKB * kKS) * (kKB * kKS);
+    const int Mp = (M + 255) / 256 * 256;  // chains zero padded (a multiple of the 128-chain stage)
     const size_t bytes = (size_t)Q * Mp;
     if (!c->xt || c->xt_rows != Q || c->xt_cols != Mp) {
         if (c->xt) cudaFree(c->xt);
@@ -327,8 +331,7 @@ int bm_launch_chain_stats_tc(bm_chains_s *c, int32_t *counts, cudaStream_t st)
         BM_CK(cudaMalloc(&c->xt, bytes));
         c->xt_rows = Q;
         c->xt_cols = Mp;
-        int rc = make_xt_map(reinterpret_cast<CUtensorMap *>(c->tmap_a), (const uint8_t *)c->xt, Q, Mp, kRows);
-        if (rc == BM_OK) rc = make_xt_map(reinterpret_cast<CUtensorMap *>(c->tmap_b), (const uint8_t *)c->xt, Q, Mp, kCols);
+        const int rc = make_xt_map(reinterpret_cast<CUtensorMap *>(c->tmap_a), (const uint8_t *)c->xt, Q, Mp, kTile);
         if (rc != BM_OK) return rc;
     }
     dim3 g1((Mp + kOtChains - 1) / kOtChains, (L + kOtSites - 1) / kOtSites);
@@ -340,8 +343,8 @@ int bm_launch_chain_stats_tc(bm_chains_s *c, int32_t *counts, cudaStream_t st)
     a.err = c->derr;
     a.L = L;
     a.q = q;
-    a.TI = kRows / q;
-    a.TJ = kCols / q;
+    a.TI = kTile / q;
+    a.TJ = kTile / q;
     a.nti = (L + a.TI - 1) / a.TI;
     a.ntj = (L + a.TJ - 1) / a.TJ;
     a.ntiles = 0;
@@ -350,11 +353,10 @@ int bm_launch_chain_stats_tc(bm_chains_s *c, int32_t *counts, cudaStream_t st)
     int dev = 0, nsm = 0;
     BM_CK(cudaGetDevice(&dev));
     BM_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const size_t smem = (size_t)kNS * (kStageA + kStageB) + (2 * kNS + 5) * 8 + 16 + 1024;
+    const size_t smem = (size_t)kNS * (kStageA + kStageB) + (size_t)kTile * kStgStride * 4 + (2 * kNS + 3) * 8 + 16 + 1024;
     BM_CK(cudaFuncSetAttribute(k_counts_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = std::min(a.ntiles, nsm);
-    k_counts_tc<<<grid, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(c->tmap_a),
-                                              *reinterpret_cast<const CUtensorMap *>(c->tmap_b), a);
+    k_counts_tc<<<grid, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(c->tmap_a), a);
     BM_CK_LAUNCH("k_counts_tc");
     return BM_OK;
 }
