@@ -263,8 +263,11 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
 /*
  * bm_energy_score -- DCA energy E(s) of n sequences (Eq. 1; Sec. 4.3: low
  * energy = good sequence).  seqs_dev: device uint8[n][L]; E_dev: device
- * float[n].  FP32 accumulation.  A symbol >= q contributes nothing to its
- * sequence's energy; the next bm_device_status then returns BM_EINVAL.
+ * float[n].  FP32 accumulation (large batches, n*L >= 3.3e6, stream J
+ * through shared memory; the sum order, and so the last bits, differ
+ * between the two forms).  A symbol >= q is flagged: the next
+ * bm_device_status returns BM_EINVAL and that sequence's energy is
+ * unspecified.
  */
 int bm_energy_score(bm_model m, const uint8_t *seqs_dev, int n, float *E_dev, void *stream);
 

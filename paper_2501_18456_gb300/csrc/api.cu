@@ -475,7 +475,7 @@ int bm_energy_score(bm_model m, const uint8_t *seqs_dev, int n, float *E_dev, vo
 {
     if (!m || (n > 0 && (!seqs_dev || !E_dev))) return bm_fail(BM_EINVAL, "bm_energy_score: NULL argument");
     if (n < 0) return bm_fail(BM_EINVAL, "bm_energy_score: n=%d < 0", n);
-    return bm_launch_energy(m->h, m->J, m->L, m->q, seqs_dev, n, E_dev, m->dflags + 4, (cudaStream_t)stream);
+    return bm_launch_energy(m, seqs_dev, n, E_dev, m->dflags + 4, (cudaStream_t)stream);
 }
 
 int bm_fields(bm_model m, const uint8_t *seqs_dev, int n, float *H_dev, int form, void *stream)

@@ -149,8 +149,10 @@ int bm_launch_update(bm_model_s *m, const float *fi, const float *fij, const int
                      int M, float lr, int want_pearson, double *partials, int nparts,
                      double *moments, cudaStream_t st);
 int bm_update_num_partials(int L);
-int bm_launch_energy(const float *h, const float *J, int L, int q, const uint8_t *seqs, int n,
-                     float *E, int *bad, cudaStream_t st);
+int bm_launch_energy(const bm_model_s *m, const uint8_t *seqs, int n, float *E, int *bad, cudaStream_t st);
+int bm_launch_energy_gather(const float *h, const float *J, int L, int q, const uint8_t *seqs, int n,
+                            float *E, int *bad, cudaStream_t st);
+int bm_launch_energy_staged(const bm_model_s *m, const uint8_t *seqs, int n, float *E, int *bad, cudaStream_t st);
 int bm_split_prepare(bm_model_s *m, int bf16, cudaStream_t st);
 int bm_split_block_sites(int L, int q);
 int bm_launch_fields_simt(const bm_model_s *m, const uint8_t *seqs, int n, float *H, cudaStream_t st);

@@ -116,8 +116,8 @@ int bm_launch_check_symbols(const uint8_t *s, size_t n, int q, int *dflag, cudaS
     return BM_OK;
 }
 
-int bm_launch_energy(const float *h, const float *J, int L, int q, const uint8_t *seqs, int n,
-                     float *E, int *bad, cudaStream_t st)
+int bm_launch_energy_gather(const float *h, const float *J, int L, int q, const uint8_t *seqs, int n,
+                            float *E, int *bad, cudaStream_t st)
 {
     if (n == 0) return BM_OK;
     const int warps = 8;
@@ -135,4 +135,16 @@ int bm_launch_mutant_scan(const float *h, const float *J, int L, int q, const ui
     k_mutant_scan<<<grid, threads, 0, st>>>(h, J, L, q, wt, dE);
     BM_CK_LAUNCH("k_mutant_scan");
     return BM_OK;
+}
+
+// Large batches use the staged form (one pass over J per CTA amortised over
+// up to 1024 sequences), smaller ones gather J rows through the caches.  The
+// staged form costs about one pass over J whatever the batch, the gather form
+// grows with n*L^2: measured crossovers lie near n*L = 3.3e6 (about 8k
+// sequences at L = 400, 13k at L = 256, 20k at L = 120).
+int bm_launch_energy(const bm_model_s *m, const uint8_t *seqs, int n, float *E, int *bad, cudaStream_t st)
+{
+    const bool staged = (double)n * m->L >= 3.3e6;
+    if (staged && bm_launch_energy_staged(m, seqs, n, E, bad, st) == BM_OK) return BM_OK;
+    return bm_launch_energy_gather(m->h, m->J, m->L, m->q, seqs, n, E, bad, st);
 }

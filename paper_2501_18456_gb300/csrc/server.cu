@@ -109,7 +109,7 @@ int launch(bm_server_s *s, Req *rq, cudaStream_t st, cudaEvent_t ev)
         uint8_t *seq = d;
         float *E = reinterpret_cast<float *>(d + round256((size_t)r.n * L));
         e = cudaMemcpyAsync(seq, r.in, (size_t)r.n * L, cudaMemcpyDefault, st);
-        if (e == cudaSuccess) rc = bm_launch_energy(m->h, m->J, L, q, seq, r.n, E, m->dflags + 4, st);
+        if (e == cudaSuccess) rc = bm_launch_energy(m, seq, r.n, E, m->dflags + 4, st);
         if (rc == BM_OK && e == cudaSuccess) e = cudaMemcpyAsync(r.out, E, (size_t)r.n * 4, cudaMemcpyDefault, st);
         break;
     }

@@ -419,7 +419,9 @@ def test_pearson_config2_full_size(bm, orc):
 
 # ---------------------------------------------------------------- energy / mutant scan
 
-@pytest.mark.parametrize("n,L,q", [(300, 16, 21), (1000, 37, 5), (0, 4, 3), (5, 1, 2), (64, 256, 21)])
+@pytest.mark.parametrize("n,L,q", [(300, 16, 21), (1000, 37, 5), (0, 4, 3), (5, 1, 2), (64, 256, 21),
+                                   # batches with n*L >= 3.3e6 take the staged form
+                                   (170000, 20, 21), (90000, 37, 5), (60000, 64, 21), (12000, 300, 21)])
 def test_energy_parity(bm, orc, n, L, q):
     h, J = synth.planted_contact_model(L, q, 3, frac=0.3) if L > 2 else synth.planted_local_model(L, q, 3)
     m = load(bm, h, J)
@@ -432,6 +434,21 @@ def test_energy_parity(bm, orc, n, L, q):
     E_o = orc.energy(h.astype(np.float64), J.astype(np.float64), S)
     scale = np.abs(h).max() * L + np.abs(J).max() * L * L / 2
     assert np.abs(E.cpu().numpy() - E_o).max() < 2e-5 * scale + 1e-6
+
+
+@pytest.mark.parametrize("n", [100, 300000])
+def test_energy_invalid_symbol_flagged(bm, n):
+    L, q = 12, 5
+    h, J = synth.planted_local_model(L, q, 3)
+    m = load(bm, h, J)
+    S = synth.random_states(n, L, q, 4)
+    S[n // 2, 3] = q + 1
+    E = torch.empty(n, dtype=torch.float32, device=DEV)
+    bm.bm_energy_score(m, to_dev(S), E)
+    with pytest.raises(bm.BmError) as e:
+        bm.bm_device_status(m)
+    assert e.value.code == bm.BM_EINVAL
+    bm.bm_device_status(m)  # cleared
 
 
 @pytest.mark.parametrize("L,q", [(16, 21), (37, 5), (256, 21), (1, 3)])
