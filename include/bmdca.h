@@ -127,6 +127,16 @@ int bm_potts_shape(bm_model m, int *L, int *q);
 int bm_chains_init(bm_model m, int M, uint64_t seed, const uint8_t *init_or_null, int where,
                    void *stream, bm_chains *out);
 
+/*
+ * bm_chains_init_shard -- chains chain0 .. chain0+M-1 of a larger ensemble
+ * (one shard per GPU when the chains are split across devices, Sec. 2.1:
+ * chains are independent).  Uniformly random start as above with the
+ * GLOBAL chain index in every Philox counter, so the shards of an ensemble
+ * draw exactly the states of one handle holding all of it: the counts of
+ * the shards sum to its counts.  The handle keeps chain0 for its sweeps.
+ */
+int bm_chains_init_shard(bm_model m, int M, uint64_t seed, uint64_t chain0, void *stream, bm_chains *out);
+
 /* Release chains.  NULL is accepted. */
 int bm_chains_free(bm_chains c);
 

@@ -51,6 +51,7 @@ SIGNATURES = {
     "bm_device_status": (_I, [_P, _P]),
     "bm_potts_shape": (_I, [_P, _P, _P]),
     "bm_chains_init": (_I, [_P, _I, _U64, _P, _I, _P, _P]),
+    "bm_chains_init_shard": (_I, [_P, _I, _U64, _U64, _P, _P]),
     "bm_chains_free": (_I, [_P]),
     "bm_chains_get": (_I, [_P, _P, _I, _P]),
     "bm_chains_set": (_I, [_P, _P, _I, _P]),
@@ -229,6 +230,13 @@ def bm_chains_init(m: Model, M: int, seed: int, init: torch.Tensor | None = None
     out = ctypes.c_void_p()
     _check(lib().bm_chains_init(m.handle, M, seed, p, where, _stream(stream), ctypes.byref(out)),
            "bm_chains_init")
+    return Chains(out, M, m.L, m.q)
+
+
+def bm_chains_init_shard(m: Model, M: int, seed: int, chain0: int, stream=None) -> Chains:
+    out = ctypes.c_void_p()
+    _check(lib().bm_chains_init_shard(m.handle, M, seed, chain0, _stream(stream), ctypes.byref(out)),
+           "bm_chains_init_shard")
     return Chains(out, M, m.L, m.q)
 
 

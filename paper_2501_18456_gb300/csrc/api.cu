@@ -194,8 +194,8 @@ int bm_model_set_engine(bm_model m, int engine)
     return BM_OK;
 }
 
-int bm_chains_init(bm_model m, int M, uint64_t seed, const uint8_t *init_or_null, int where,
-                   void *stream, bm_chains *out)
+static int chains_init(bm_model m, int M, uint64_t seed, uint64_t chain0, const uint8_t *init_or_null, int where,
+                       void *stream, bm_chains *out)
 {
     if (!out) return bm_fail(BM_EINVAL, "bm_chains_init: out is NULL");
     *out = nullptr;
@@ -211,6 +211,7 @@ int bm_chains_init(bm_model m, int M, uint64_t seed, const uint8_t *init_or_null
     c->device = m->device;
     c->seed = seed;
     c->sweep = 0;
+    c->chain0 = chain0;
     const size_t n = (size_t)M * m->L;
     cudaError_t e = cudaMalloc(&c->s, n);
     if (e == cudaSuccess) e = cudaMalloc(&c->derr, sizeof(int));
@@ -234,7 +235,7 @@ int bm_chains_init(bm_model m, int M, uint64_t seed, const uint8_t *init_or_null
         }
         if (rc == BM_OK && bad) rc = bm_fail(BM_EINVAL, "bm_chains_init: symbol >= q in init");
     } else {
-        rc = bm_launch_chains_init(c->s, M, m->L, m->q, seed, st);
+        rc = bm_launch_chains_init(c->s, M, m->L, m->q, seed, chain0, st);
     }
     if (rc != BM_OK) {
         cudaFree(c->s);
@@ -244,6 +245,17 @@ int bm_chains_init(bm_model m, int M, uint64_t seed, const uint8_t *init_or_null
     }
     *out = c;
     return BM_OK;
+}
+
+int bm_chains_init(bm_model m, int M, uint64_t seed, const uint8_t *init_or_null, int where,
+                   void *stream, bm_chains *out)
+{
+    return chains_init(m, M, seed, 0, init_or_null, where, stream, out);
+}
+
+int bm_chains_init_shard(bm_model m, int M, uint64_t seed, uint64_t chain0, void *stream, bm_chains *out)
+{
+    return chains_init(m, M, seed, chain0, nullptr, BM_DEVICE, stream, out);
 }
 
 int bm_chains_free(bm_chains c)

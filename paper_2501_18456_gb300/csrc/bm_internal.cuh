@@ -53,6 +53,7 @@ struct bm_chains_s {
     uint8_t *s = nullptr;  // [M][L]
     uint64_t seed = 0;
     uint64_t sweep = 0;    // Philox sweep word of the next sweep
+    uint64_t chain0 = 0;   // global index of chain 0 (shards of a larger ensemble)
     int stats_engine = BM_STATS_AUTO;
     int *derr = nullptr;   // device error word of this handle's kernels
     // Transposed FP8 one-hot of the states for the tensor-core counts
@@ -125,7 +126,7 @@ __host__ __device__ __forceinline__ size_t bm_pair_block(int L, int i, int j)
 int bm_launch_check_model(const float *h, const float *J, int L, int q, int *dflags,
                           cudaStream_t st);
 int bm_launch_check_symbols(const uint8_t *s, size_t n, int q, int *dflag, cudaStream_t st);
-int bm_launch_chains_init(uint8_t *s, int M, int L, int q, uint64_t seed, cudaStream_t st);
+int bm_launch_chains_init(uint8_t *s, int M, int L, int q, uint64_t seed, uint64_t chain0, cudaStream_t st);
 int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M);
 int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
 int bm_gather_block_stride(int q);

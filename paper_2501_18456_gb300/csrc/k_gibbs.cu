@@ -33,13 +33,13 @@
 
 namespace {
 
-__global__ void k_chains_init(uint8_t *__restrict__ s, int M, int L, int q, uint64_t seed)
+__global__ void k_chains_init(uint8_t *__restrict__ s, int M, int L, int q, uint64_t seed, uint64_t chain0)
 {
     const size_t n = (size_t)M * L;
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (size_t)gridDim.x * blockDim.x) {
         const uint64_t m = t / (size_t)L, i = t % (size_t)L;
-        const uint64_t r = bm_u24(seed, m, 0, i, 1);
+        const uint64_t r = bm_u24(seed, chain0 + m, 0, i, 1);
         s[t] = (uint8_t)((r * (uint64_t)q) >> 24);
     }
 }
@@ -165,7 +165,7 @@ struct GibbsArgs {
     const float *Jg;
     uint8_t *states;
     int *err;
-    uint64_t seed, sweep0;
+    uint64_t seed, sweep0, chain0;  // chain0: global index of chain 0 (Philox counter)
     float beta;
     int M, L, q, Lp, bs, jc, nch, ns, cpc, nsweeps;
 };
@@ -175,7 +175,7 @@ struct GibbsArgs {
 // the launch's common shape) and the index of its first chain.
 struct BatchItem {
     GibbsArgs a;
-    long long chain0;
+    long long first;  // first chain of the tile (index into the model's chains)
 };
 
 // Shared memory: [ns stages of jc*bs floats][cpc x Lp u32 row offsets]
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(1024, 1) k_gibbs_staged(const GibbsArgs p0, co
     constexpr int G = 32 / GW;
     // batched launch: this CTA's model and first chain come from the work list
     const GibbsArgs p = BATCH ? items[blockIdx.x].a : p0;
-    const size_t cta0 = BATCH ? (size_t)items[blockIdx.x].chain0 : (size_t)blockIdx.x * p0.cpc;
+    const size_t cta0 = BATCH ? (size_t)items[blockIdx.x].first : (size_t)blockIdx.x * p0.cpc;
     extern __shared__ __align__(128) unsigned char smem[];
     const int nwc = (blockDim.x >> 5) - 1;  // consumer warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(1024, 1) k_gibbs_staged(const GibbsArgs p0, co
                 const float w = (a < q) ? expf(e - mx) : 0.0f;
                 const float S = group_inclusive_scan<GW>(w, a);
                 const float tot = __shfl_sync(0xffffffffu, S, q - 1, GW);
-                const uint64_t m = cta0 + slot0 + r;
+                const uint64_t m = p.chain0 + cta0 + slot0 + r;  // global chain index
                 const uint32_t r24 = bm_u24(p.seed, m, sweep, (uint64_t)i, 0);
                 const float thr = ((float)r24 * 5.9604644775390625e-8f) * tot;  // u * S_total
                 const unsigned bal = __ballot_sync(0xffffffffu, (a < q) && (thr < S)) & gmask;
@@ -424,11 +424,11 @@ int dispatch_shape(const GibbsArgs &a, const Shape &s, cudaStream_t st, const Ba
 
 }  // namespace
 
-int bm_launch_chains_init(uint8_t *s, int M, int L, int q, uint64_t seed, cudaStream_t st)
+int bm_launch_chains_init(uint8_t *s, int M, int L, int q, uint64_t seed, uint64_t chain0, cudaStream_t st)
 {
     const size_t n = (size_t)M * L;
     const int grid = (int)std::min<size_t>((n + 255) / 256, 65535);
-    k_chains_init<<<grid, 256, 0, st>>>(s, M, L, q, seed);
+    k_chains_init<<<grid, 256, 0, st>>>(s, M, L, q, seed, chain0);
     BM_CK_LAUNCH("k_chains_init");
     return BM_OK;
 }
@@ -454,6 +454,7 @@ int bm_launch_gibbs_simt(const bm_model_s *m, bm_chains_s *c, int nsweeps, float
     a.states = c->s;
     a.err = m->dflags + 3;
     a.seed = c->seed;
+    a.chain0 = c->chain0;
     a.sweep0 = c->sweep;
     a.beta = beta;
     a.M = c->M;
@@ -557,6 +558,7 @@ void fill_items(const bm_batch_s *b, BatchItem *dst, int nsweeps, float beta, ui
         a.states = states_override ? states_override[k] : c->s;
         a.err = m->dflags + 3;
         a.seed = c->seed;
+        a.chain0 = c->chain0;
         a.sweep0 = c->sweep;
         a.beta = beta;
         a.M = c->M;
@@ -569,7 +571,7 @@ void fill_items(const bm_batch_s *b, BatchItem *dst, int nsweeps, float beta, ui
         a.ns = s.ns;
         a.cpc = s.cpc;
         a.nsweeps = nsweeps;
-        dst[t].chain0 = b->first[t];
+        dst[t].first = b->first[t];
     }
 }
 

@@ -225,7 +225,7 @@ struct MmaArgs {
     const float *Jg;  // gather layout (in-block corrections): Jg[i][j][b][a], block stride bs
     uint8_t *states;
     int *err;
-    uint64_t seed, sweep0;
+    uint64_t seed, sweep0, chain0;  // chain0: global index of chain 0 (Philox counter)
     float beta;
     int M, L, q, Lp, bs, B, nb, nK, X, NC, nsweeps;
     long long nblocks;
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                 named_bar(1, 128);
                 const int i = g.i0 + pp;
                 for (int ch = w; ch < NC; ch += 128) {
-                    const uint64_t m = cta0 + ch;
+                    const uint64_t m = p.chain0 + cta0 + ch;  // global chain index
                     float H[32];
 #pragma unroll
                     for (int a = 0; a < 32; ++a)
@@ -905,6 +905,7 @@ int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, 
     a.states = c->s;
     a.err = m->dflags + 3;
     a.seed = c->seed;
+    a.chain0 = c->chain0;
     a.sweep0 = c->sweep;
     a.beta = beta;
     a.M = c->M;

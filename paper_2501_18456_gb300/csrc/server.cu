@@ -100,7 +100,7 @@ int launch(bm_server_s *s, Req *rq, cudaStream_t st, cudaEvent_t ev)
         c.s = d;
         c.seed = r.seed;
         c.sweep = 0;
-        rc = bm_launch_chains_init(c.s, r.n, L, q, r.seed, st);
+        rc = bm_launch_chains_init(c.s, r.n, L, q, r.seed, 0, st);
         if (rc == BM_OK) rc = bm_sweep_run(m, &c, r.nsweeps, r.beta, st);
         if (rc == BM_OK) e = cudaMemcpyAsync(r.out, c.s, (size_t)r.n * L, cudaMemcpyDefault, st);
         break;

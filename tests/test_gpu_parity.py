@@ -467,3 +467,34 @@ def test_mutant_scan_parity(bm, orc, L, q):
     bm.bm_mutant_scan(m, to_dev(wt), dE2)  # device wild type
     torch.cuda.synchronize()
     assert torch.equal(dE2.cpu(), dE.cpu())
+
+
+# ---------------------------------------------------------------- sharding
+
+@pytest.mark.parametrize("engine", GIBBS_ENGINES)
+def test_shards_reproduce_the_full_ensemble(bm, engine):
+    """Chains split into shards with global chain indices draw the states of
+    one handle holding all of them, and their counts sum to its counts."""
+    from paper_2501_18456_gb300 import sharding
+    L, q, M = 40, 21, 700
+    h, J = synth.planted_local_model(L, q, 6, sigma_h=1.0, sigma_J=0.3)
+    m = load(bm, h, J, engine)
+    full = bm.bm_chains_init(m, M, 55)
+    bm.bm_gibbs_sweep(m, full, 4, 1.0)
+    shards = []
+    for r in range(3):
+        first, n = sharding.shard_range(M, r, 3)
+        c = bm.bm_chains_init_shard(m, n, 55, first)
+        bm.bm_gibbs_sweep(m, c, 4, 1.0)
+        shards.append(c)
+    bm.bm_device_status(m)
+    assert np.array_equal(np.concatenate([states_of(bm, c) for c in shards]), states_of(bm, full))
+    tot = torch.zeros((bm.n_blocks(L), q, q), dtype=torch.int32, device=DEV)
+    part = torch.empty_like(tot)
+    for c in shards:
+        bm.bm_chain_stats(c, part)
+        tot += part
+    ref = torch.empty_like(tot)
+    bm.bm_chain_stats(full, ref)
+    torch.cuda.synchronize()
+    assert torch.equal(tot, ref)
