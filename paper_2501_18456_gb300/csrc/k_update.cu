@@ -6,10 +6,13 @@
 //   J'_ij(a,b) = J_ij(a,b) + lr (f_ij(a,b) - p_ij(a,b))  written to (i,j,a,b)
 //                                                        and (j,i,b,a)
 //   x = f_ij - f_i f_j,  y = p_ij - p_i p_j              (connected correlations)
-// and accumulates sum x, y, x^2, y^2, xy in FP64 (x and y themselves are
-// FP32, the precision of their inputs).  Per-CTA partial moments go to a
-// scratch array that a single-CTA kernel sums in a fixed order, so the
-// result is deterministic.  The new parameters go to the back buffer; the
+// and accumulates sum x, y, x^2, y^2, xy (x and y themselves are FP32, the
+// precision of their inputs): within a pair each lane adds its terms with
+// Kahan-compensated FP32 sums, and the pairs are reduced in FP64.  The
+// transposed (j,i) copy goes through a per-warp shared-memory tile so both
+// writes are coalesced.  Per-CTA partial moments go to a scratch array that
+// a single-CTA kernel sums in a fixed order, so the result is
+// deterministic.  The new parameters go to the back buffer; the
 // host decides whether to swap it in.
 #include "bm_internal.cuh"
 
@@ -22,8 +25,9 @@ constexpr int kUpdWarps = 8;
 __device__ __forceinline__ void pair_from_index(long long p, int L, int &i, int &j)
 {
     // Rows i hold L-1-i pairs; start(i) = i*(2L-i-1)/2.
-    const double tL = 2.0 * L - 1.0;
-    int r = (int)floor((tL - sqrt(tL * tL - 8.0 * (double)p)) * 0.5);
+    // FP32 estimate of the row; the two loops below make it exact
+    const float tL = 2.0f * (float)L - 1.0f;
+    int r = (int)floorf((tL - sqrtf(fmaxf(tL * tL - 8.0f * (float)p, 0.0f))) * 0.5f);
     if (r < 0) r = 0;
     if (r > L - 2) r = L - 2;
     auto start = [L](long long rr) { return rr * (2LL * L - rr - 1) / 2; };
@@ -33,41 +37,80 @@ __device__ __forceinline__ void pair_from_index(long long p, int L, int &i, int 
     j = (int)(p - start(r)) + r + 1;
 }
 
+// Kahan-compensated FP32 accumulator: s - c carries the sum to about one
+// ulp whatever the number of terms (used for the ~q*q/32 terms a lane adds
+// per pair before the FP64 reduction across pairs).
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 __global__ void __launch_bounds__(kUpdWarps * 32) k_update_pairs(
     const float *__restrict__ J, float *__restrict__ Jn, const float *__restrict__ fi,
     const float *__restrict__ fij, const int32_t *__restrict__ C, int L, int q, float invM,
     float lr, int want_pearson, double *__restrict__ partials)
 {
+    // per warp: the new (i,j) block for its transposed copy (row stride 33:
+    // conflict-free both ways), and the pair's one-site vectors
+    __shared__ float tile[kUpdWarps][32 * 33];
+    __shared__ float vec[kUpdWarps][4][32];  // p_i(a), p_j(b), f_i(a), f_j(b)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int qq = q * q;
     const long long P = (long long)L * (L - 1) / 2;
+    float *tw = tile[warp];
     double sx = 0.0, sy = 0.0, sxx = 0.0, syy = 0.0, sxy = 0.0;
     for (long long p = (long long)blockIdx.x * kUpdWarps + warp; p < P;
          p += (long long)gridDim.x * kUpdWarps) {
         int i, j;
         pair_from_index(p, L, i, j);
         const size_t blk = bm_pair_block(L, i, j) * qq;
-        const size_t di = bm_pair_block(L, i, i) * qq, dj = bm_pair_block(L, j, j) * qq;
         const size_t ij = ((size_t)i * L + j) * qq, ji = ((size_t)j * L + i) * qq;
+        if (want_pearson && lane < q) {
+            vec[warp][0][lane] = (float)C[bm_pair_block(L, i, i) * qq + (size_t)lane * (q + 1)] * invM;
+            vec[warp][1][lane] = (float)C[bm_pair_block(L, j, j) * qq + (size_t)lane * (q + 1)] * invM;
+            vec[warp][2][lane] = fi[(size_t)i * q + lane];
+            vec[warp][3][lane] = fi[(size_t)j * q + lane];
+        }
+        __syncwarp();
+        Kahan kx, ky, kxx, kyy, kxy;
+#pragma unroll 4
         for (int e = lane; e < qq; e += 32) {
             const int a = e / q, b = e - a * q;
             const float f = fij[ij + e];
             const float pij = (float)C[blk + e] * invM;
             const float v = fmaf(lr, f - pij, J[ij + e]);
             Jn[ij + e] = v;
-            Jn[ji + (size_t)b * q + a] = v;
+            tw[a * 33 + b] = v;
             if (want_pearson) {
-                const float pa = (float)C[di + (size_t)a * q + a] * invM;
-                const float pb = (float)C[dj + (size_t)b * q + b] * invM;
-                const float x = fmaf(-fi[(size_t)i * q + a], fi[(size_t)j * q + b], f);
-                const float y = fmaf(-pa, pb, pij);
-                const double dx = x, dy = y;
-                sx += dx;
-                sy += dy;
-                sxx = fma(dx, dx, sxx);
-                syy = fma(dy, dy, syy);
-                sxy = fma(dx, dy, sxy);
+                const float x = fmaf(-vec[warp][2][a], vec[warp][3][b], f);
+                const float y = fmaf(-vec[warp][0][a], vec[warp][1][b], pij);
+                kx.add(x);
+                ky.add(y);
+                kxx.add(x * x);
+                kyy.add(y * y);
+                kxy.add(x * y);
             }
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int e = lane; e < qq; e += 32) {  // (j,i) block: element (b,a) = J'_ij(a,b)
+            const int b = e / q, a = e - b * q;
+            Jn[ji + e] = tw[a * 33 + b];
+        }
+        __syncwarp();  // tile and vec are rewritten by the next pair
+        if (want_pearson) {
+            sx += kx.value();
+            sy += ky.value();
+            sxx += kxx.value();
+            syy += kyy.value();
+            sxy += kxy.value();
         }
     }
     if (!want_pearson) return;
