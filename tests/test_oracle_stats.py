@@ -195,3 +195,75 @@ def test_update_fixed_point(orc):
     J = np.zeros((L, L, q, q))
     h2, J2 = orc.update(h, J, fi, fij, orc.chain_stats(S, q), M, 0.3)
     assert np.allclose(h2, h, atol=1e-15) and np.allclose(J2, 0, atol=1e-15)
+
+
+def all_states(L, q):
+    return np.array(np.meshgrid(*[np.arange(q)] * L, indexing="ij")).reshape(L, -1).T.astype(np.uint8)
+
+
+def exact_log_likelihood(orc, h, J, msa, S_all):
+    """Mean of -E over the data minus log Z, Z by enumeration of all q^L states."""
+    e_all = -orc.energy(h, J, S_all)
+    top = e_all.max()
+    return float(-orc.energy(h, J, msa).mean() - (top + np.log(np.exp(e_all - top).sum())))
+
+
+@pytest.mark.parametrize("point", ["uniform", "integer_weights"])
+def test_update_is_log_likelihood_gradient(orc, point):
+    """Eq. 5 is gradient ascent on the data log-likelihood.  When the chain
+    ensemble holds the model's marginals exactly, (theta' - theta) / lr must
+    equal the central finite difference of the log-likelihood computed by
+    enumeration from energies alone.  A coupling J_ij(a, b) is tied to
+    J_ji(b, a), so both move together.  This pins the sign of the step, the
+    pair indexing and the transposed half of J without restating Eq. 5.
+    Exact model marginals: at theta = 0 the chain ensemble is every state
+    once; at a model whose Boltzmann weights exp(-E) are integers it is every
+    state repeated by its weight."""
+    L, q = 3, 3
+    S_all = all_states(L, q)
+    rng = np.random.default_rng(5)
+    h = np.zeros((L, q))
+    J = np.zeros((L, L, q, q))
+    if point == "uniform":
+        chains = S_all
+    else:
+        h = np.log(rng.integers(1, 4, size=(L, q)).astype(np.float64))
+        for i in range(L):
+            for j in range(i + 1, L):
+                B = np.log(rng.integers(1, 3, size=(q, q)).astype(np.float64))
+                J[i, j], J[j, i] = B, B.T
+        w = np.exp(-orc.energy(h, J, S_all))
+        mult = np.rint(w).astype(np.int64)
+        assert np.allclose(w, mult, rtol=1e-12, atol=0) and mult.min() >= 1
+        chains = np.repeat(S_all, mult, axis=0)
+    M = chains.shape[0]
+    msa = synth.random_states(40, L, q, 6)
+    fi, fij = orc.data_stats(msa, None, q, 0.0)
+    lr = 0.1
+    h2, J2 = orc.update(h, J, fi, fij, orc.chain_stats(chains, q), M, lr)
+    eps = 1e-5
+
+    def grad(hp, Jp, hm, Jm):
+        return (exact_log_likelihood(orc, hp, Jp, msa, S_all)
+                - exact_log_likelihood(orc, hm, Jm, msa, S_all)) / (2 * eps)
+
+    for i in range(L):
+        for a in range(q):
+            hp, hm = h.copy(), h.copy()
+            hp[i, a] += eps
+            hm[i, a] -= eps
+            assert abs((h2[i, a] - h[i, a]) / lr - grad(hp, J, hm, J)) < 1e-7
+    for i in range(L):
+        for j in range(i + 1, L):
+            for a in range(q):
+                for b in range(q):
+                    Jp, Jm = J.copy(), J.copy()
+                    Jp[i, j, a, b] += eps
+                    Jp[j, i, b, a] += eps
+                    Jm[i, j, a, b] -= eps
+                    Jm[j, i, b, a] -= eps
+                    g = grad(h, Jp, h, Jm)
+                    assert abs((J2[i, j, a, b] - J[i, j, a, b]) / lr - g) < 1e-7
+                    assert abs((J2[j, i, b, a] - J[j, i, b, a]) / lr - g) < 1e-7
+    # the step is not vacuous: the data differ from the model
+    assert np.abs(h2 - h).max() > 1e-3 and np.abs(J2 - J).max() > 1e-3
