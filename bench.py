@@ -40,10 +40,10 @@ L_SITES, Q, M_CHAINS, N_SEQS, NSWEEPS, LR, SEED = 256, 21, 10000, 50000, 10, 0.0
 WORKLOAD = "bmDCA dense protein-like: L=256 q=21 M=10000 chains, 10 sweeps/iter, MSA N=50000"
 METRIC = "Gibbs site-updates/s (L=256,q=21,M=10k)"
 UNIT = "site-updates/s"
-# DRAM bytes per launch of k_gibbs_mma (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of this bench's 10-sweep launch);
-# set to None whenever the kernel changes until it is captured again.
-TRAFFIC_GIBBS_MMA = 1189350656 + 3484160
+# DRAM bytes per 10-sweep launch of each sweep kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of this bench's launch); None
+# whenever the kernel has changed since it was captured.
+TRAFFIC_GIBBS = {"k_gibbs_mma": 1189350656 + 3484160, "k_gibbs_pair": None}
 
 
 def parse():
@@ -326,9 +326,12 @@ def run_ours(args, rank, world, local):
     Qd = float(L_SITES * Q)
     flops_per_launch = 2.0 * 2.0 * M_CHAINS * Qd * Qd * NSWEEPS
     achieved = flops_per_launch / (ms_gibbs * 1e-3) / 1e12
+    bmdca.bm_model_set_engine(model, bmdca.BM_ENGINE_AUTO)
+    form = bmdca.bm_model_sweep_engine(model, M_CHAINS)
+    kname = {bmdca.BM_ENGINE_MMA_PAIR: "k_gibbs_pair", bmdca.BM_ENGINE_MMA: "k_gibbs_mma"}.get(form, "k_gibbs_staged")
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf, "traffic": TRAFFIC_GIBBS_MMA,
-                "kernel": "k_gibbs_mma",
+                "frac": achieved / peak_tf, "traffic": TRAFFIC_GIBBS.get(kname),
+                "kernel": kname,
                 "note": "achieved = 2 passes (fp16 hi, lo) x 2*M*(L*q)^2 flops per sweep x sweeps per "
                         "launch / CUDA-event launch time; peak: " + peak_src +
                         "; fp16 and bf16 share the dense rate"}

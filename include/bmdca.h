@@ -67,9 +67,14 @@ enum { BM_HOST = 0, BM_DEVICE = 1 };
 /* Which kernel form bm_gibbs_sweep uses (bm_model_set_engine). */
 enum {
     BM_ENGINE_SIMT = 0,  /* FP32 CUDA-core gather of J rows */
-    BM_ENGINE_AUTO = 1,  /* default: tensor cores when q >= 10 and the shape fits, else CUDA
+    BM_ENGINE_AUTO = 1,  /* default: tensor cores when q >= 10 and the shape fits (the
+                            two-CTA form when it fits, else the one-CTA form), else CUDA
                             cores (the measured faster form on each side of the crossover) */
-    BM_ENGINE_MMA = 2    /* tensor cores: one-hot x (fp16 hi + fp16 lo) J, FP32 accumulate */
+    BM_ENGINE_MMA = 2,   /* tensor cores: one-hot x (fp16 hi + fp16 lo) J, FP32 accumulate;
+                            one CTA per SM computes both blocks of a block pair */
+    BM_ENGINE_MMA_PAIR = 3  /* the same arithmetic split over the two CTAs of a cluster: each
+                               CTA streams and redraws every other site block, the new states
+                               are exchanged through distributed shared memory */
 };
 
 /* Library version string, e.g. "bmdca-gb300 0.1". */
@@ -170,6 +175,12 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
 /* Select the kernel form used by bm_gibbs_sweep for this model
  * (BM_ENGINE_*).  BM_EINVAL for an unknown engine. */
 int bm_model_set_engine(bm_model m, int engine);
+
+/* The kernel form bm_gibbs_sweep runs for this model and M chains, with
+ * BM_ENGINE_AUTO resolved: BM_ENGINE_SIMT, BM_ENGINE_MMA or
+ * BM_ENGINE_MMA_PAIR, written to *engine_out.  BM_EINVAL for a NULL
+ * argument or M < 1.  May query the device (cluster occupancy). */
+int bm_model_sweep_engine(bm_model m, int M, int *engine_out);
 
 /* Kernel form used by bm_chain_stats (bm_chains_set_stats_engine). */
 enum {

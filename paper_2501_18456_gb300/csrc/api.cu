@@ -32,6 +32,7 @@ void free_model(bm_model_s *m)
     cudaFree(m->Jg);
     cudaFree(m->Jt);
     cudaFree(m->Jt_bf);
+    cudaFree(m->Jc);
     cudaFree(m->dflags);
     cudaFree(m->dred);
     delete m;
@@ -159,6 +160,7 @@ int bm_potts_set(bm_model m, const float *h, const float *J, int where, void *st
         BM_CK(cudaMemcpyAsync(m->J, J, nJ * sizeof(float), copy_kind(where, BM_DEVICE), st));
         m->mma_current = false;
         m->bf_current = false;
+        m->corr_current = false;
         return bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
     }
     return BM_OK;
@@ -188,9 +190,18 @@ int bm_potts_shape(bm_model m, int *L, int *q)
 int bm_model_set_engine(bm_model m, int engine)
 {
     if (!m) return bm_fail(BM_EINVAL, "bm_model_set_engine: NULL model");
-    if (engine != BM_ENGINE_SIMT && engine != BM_ENGINE_AUTO && engine != BM_ENGINE_MMA)
+    if (engine != BM_ENGINE_SIMT && engine != BM_ENGINE_AUTO && engine != BM_ENGINE_MMA &&
+        engine != BM_ENGINE_MMA_PAIR)
         return bm_fail(BM_EINVAL, "bm_model_set_engine: unknown engine %d", engine);
     m->engine = engine;
+    return BM_OK;
+}
+
+int bm_model_sweep_engine(bm_model m, int M, int *engine_out)
+{
+    if (!m || !engine_out || M < 1) return bm_fail(BM_EINVAL, "bm_model_sweep_engine: bad argument");
+    const int form = bm_sweep_form(m, M);
+    *engine_out = form == 2 ? BM_ENGINE_MMA_PAIR : form == 1 ? BM_ENGINE_MMA : BM_ENGINE_SIMT;
     return BM_OK;
 }
 
@@ -344,16 +355,34 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
 
 }  // extern "C"
 
+int bm_sweep_form(const bm_model_s *m, int M)
+{
+    if (m->engine == BM_ENGINE_MMA_PAIR) return 2;
+    if (m->engine == BM_ENGINE_MMA) return 1;
+    if (m->engine != BM_ENGINE_AUTO) return 0;
+    // AUTO: the tensor-core sweep from q = 10 up (measured crossover between
+    // q = 8 and q = 12 at L = 256: the one-hot contraction does q times the
+    // gather's arithmetic and small alphabets make long sequential blocks);
+    // the two-CTA form (half the coupling bytes per SM) unless it needs more
+    // waves of CTAs than the one-CTA form (long sequences leave room for
+    // fewer chains per CTA).
+    if (m->q < 10) return 0;
+    const int nc1 = bm_gibbs_mma_chains_per_cta(m, M);
+    const int w2 = bm_gibbs_pair_waves(m, M);
+    if (nc1 == 0) return w2 > 0 ? 2 : 0;
+    const int nsm = m->num_sms > 0 ? m->num_sms : 1;
+    const int w1 = ((M + nc1 - 1) / nc1 + nsm - 1) / nsm;
+    return (w2 > 0 && w2 <= w1) ? 2 : 1;
+}
+
 int bm_sweep_run(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)
 {
+    const int form = bm_sweep_form(m, c->M);
     for (int done = 0; done < nsweeps;) {
         const int k = nsweeps - done < kMaxSweepsPerLaunch ? nsweeps - done : kMaxSweepsPerLaunch;
-        // AUTO: the tensor-core sweep from q = 10 up (measured crossover between
-        // q = 8 and q = 12 at L = 256: the one-hot contraction does q times the
-        // gather's arithmetic and small alphabets make long sequential blocks).
-        const bool mma = m->engine == BM_ENGINE_MMA ||
-                         (m->engine == BM_ENGINE_AUTO && m->q >= 10 && bm_gibbs_mma_chains_per_cta(m, c->M) > 0);
-        const int rc = mma ? bm_launch_gibbs_mma(m, c, k, beta, st) : bm_launch_gibbs_simt(m, c, k, beta, st);
+        const int rc = form == 2   ? bm_launch_gibbs_pair(m, c, k, beta, st)
+                       : form == 1 ? bm_launch_gibbs_mma(m, c, k, beta, st)
+                                   : bm_launch_gibbs_simt(m, c, k, beta, st);
         if (rc != BM_OK) return rc;
         c->sweep += (uint64_t)k;
         done += k;
@@ -476,6 +505,7 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
         t = m->J; m->J = m->J_back; m->J_back = t;
         m->mma_current = false;
         m->bf_current = false;
+        m->corr_current = false;
         rc = bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
         if (rc != BM_OK) return rc;
     }

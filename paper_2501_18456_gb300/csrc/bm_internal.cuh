@@ -27,13 +27,22 @@ struct bm_model_s {
     // block (rows (i,a) of the block, zero padded), Kp columns (j,b) (zero
     // padded to a multiple of 64) in 64-column slabs with hi and lo
     // interleaved, and two TMA tensor maps over it (CUtensorMap, 128 bytes
-    // each): 256-row boxes of both slabs (two consecutive blocks) and
-    // 128-row boxes of one slab.  Rebuilt lazily when stale.
+    // each): 256-row boxes of both slabs (two consecutive blocks),
+    // 128-row boxes of one slab, and 128-row boxes of both slabs (one
+    // block's hi and lo tiles).  Rebuilt lazily when stale.
     void *Jt = nullptr;
     int Kp = 0;
     bool mma_current = false;
     alignas(64) unsigned char tmap_j[128] = {};
     alignas(64) unsigned char tmap_j1[128] = {};
+    alignas(64) unsigned char tmap_jp[128] = {};
+    // In-block coupling blocks for the two-CTA sweep's corrections: for
+    // site block k (B sites, B = the tensor-core block size) and each pair
+    // pi > pj of its sites (slot pi*(pi-1)/2 + pj), J_ij(a, b) at
+    // Jc[k][slot][b][a] with rows padded to q4 = q rounded up to 4 floats
+    // (zeros beyond q and beyond L).  Rebuilt lazily when stale.
+    float *Jc = nullptr;
+    bool corr_current = false;
     // The same layout with bf16 hi/lo parts (split-precision fields), its
     // 128-row one-slab tensor map, and its staleness flag.
     void *Jt_bf = nullptr;
@@ -129,6 +138,12 @@ int bm_launch_check_symbols(const uint8_t *s, size_t n, int q, int *dflag, cudaS
 int bm_launch_chains_init(uint8_t *s, int M, int L, int q, uint64_t seed, uint64_t chain0, cudaStream_t st);
 int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M);
 int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
+int bm_gibbs_pair_chains_per_cluster(const bm_model_s *m, int M);
+int bm_gibbs_pair_waves(const bm_model_s *m, int M);
+int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
+// Tensor-core sweep form for this model and chain count: 2 = two-CTA
+// clusters, 1 = one CTA, 0 = CUDA cores (the model's engine, AUTO resolved).
+int bm_sweep_form(const bm_model_s *m, int M);
 int bm_gather_block_stride(int q);
 int bm_launch_build_gather(const float *J, float *Jg, int L, int q, cudaStream_t st);
 int bm_launch_gibbs_simt(const bm_model_s *m, bm_chains_s *c, int nsweeps, float beta,

@@ -811,7 +811,7 @@ EncodeTiledFn encode_fn()
 // (stride 2*Kp*2 bytes), dim 2 = slab index 2*(k/64) + {0 hi, 1 lo} (stride
 // 128 bytes), 128B swizzle.  box_rows x box_slabs per op: {256, 2} lands
 // the hi tiles of two consecutive blocks and then their lo tiles; {128, 1}
-// one tile.
+// one tile; {128, 2} one block's hi tile and then its lo tile.
 int make_map(CUtensorMap *map, const void *ptr, int rows, int Kp, int box_rows, int box_slabs,
              CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16)
 {
@@ -877,6 +877,7 @@ int bm_split_prepare(bm_model_s *m, int bf16, cudaStream_t st)
         } else {
             rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_j), *buf, rows, Kp, 2 * kRowsA, 2);
             if (rc == BM_OK) rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_j1), *buf, rows, Kp, kRowsA, 1);
+            if (rc == BM_OK) rc = make_map(reinterpret_cast<CUtensorMap *>(m->tmap_jp), *buf, rows, Kp, kRowsA, 2);
         }
         if (rc != BM_OK) return rc;
     }

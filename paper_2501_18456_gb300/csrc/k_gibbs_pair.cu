@@ -1,0 +1,859 @@
+// Persistent-chain Gibbs sweeps on the 5th-generation tensor cores, split
+// over the two CTAs of a thread-block cluster.
+//
+// Method: Sec. 2.1 ("Monte Carlo estimation of the gradient"), sweep = every
+// site once in order (Sec. 3.3).  The arithmetic is that of the single-CTA
+// tensor-core sweep (k_gibbs_mma.cu): sites in blocks of B = floor(128/q),
+// the fields of a block's 128 rows (i,a) as the contraction of the coupling
+// rows (fp16 hi + fp16 lo, FP32 accumulation in TMEM) with the one-hot
+// states, then an exact sequential redraw of the block's sites with in-block
+// corrections, blocks taken in pairs (2P, 2P+1).
+//
+// Split.  Both CTAs of a cluster hold the same NC chains, each a full copy of
+// their states in its shared memory.  CTA r owns the blocks 2P + r: it loads
+// only their coupling rows (one 32 KB TMA op per 64-column K chunk: the hi
+// and lo tiles of 128 rows), accumulates only their fields and redraws only
+// them.  Compared with one CTA doing both blocks of a pair for NC/2 chains,
+// each SM moves half the coupling bytes per chunk through shared memory and
+// its MMAs are twice as wide (N = NC), so the shared-memory bandwidth that
+// bounds the single-CTA form buys about twice the MMA work per byte.
+//
+// Exchange.  Each new state a drawer picks is also stored into the peer's
+// copy (st.shared::cluster).  After a block every drawer thread arrives on
+// the peer's ready barrier of that block's parity with release semantics at
+// cluster scope; waiters acquire at cluster scope.  Schedule of pair P in
+// CTA r, each step a run of 64-column K chunks:
+//   A  main chunks [0, X) into block 2P+r: states after block 2P-3, with
+//      blocks 2P-2 and 2P-1 (being redrawn) from their pre-redraw snapshots;
+//   B  (CTA 1 only) delta chunks of block 2P-2 (+1 at the new, -1 at the old
+//      state of each changed site) into block 2P-1, once block 2P-2's states
+//      arrived from CTA 0; this completes block 2P-1;
+//   C  main chunks [X, nK) into block 2P+r;
+//   D  delta chunks of blocks 2P-2 and 2P-1 into block 2P+r; this completes
+//      block 2P in CTA 0 (block 2P+1 is completed by step B of pair P+1).
+// Snapshots (a block's states before its redraw; used for the blocks being
+// redrawn during the main chunks, for the delta chunks and for the in-block
+// corrections) of pair (2P+2, 2P+3) are taken in each CTA while no CTA can
+// be writing those sites: in CTA 1 right after it redrew block 2P+1 and
+// before it publishes it; in CTA 0 once block 2P+1 has arrived and before
+// CTA 0 redraws block 2P+2 (its generator waits for them at step D).
+//
+// Data path per CTA (one CTA per SM, NC <= 160 chains, NC a multiple of 16):
+//   warp 0       TMA producer (3-slot ring of 32 KB coupling tiles);
+//   warp 1       TMEM allocation (two accumulators of NC columns, own block
+//                j = kb/2 in slot j % 2) and the single MMA-issuing thread
+//                (M = 128 rows, N = NC chains, K = 16, hi and lo);
+//   warps 2-6    drawers, one thread per chain (warps 2-5 read the four TMEM
+//                lane quarters of a site's rows into shared memory);
+//   warps 7-11   generators of the one-hot operand tiles (2-slot ring), one
+//                thread per chain (zero the row, then store its few nonzeros).
+// Every wait is bounded by %globaltimer (2 s); a timeout sets the CTA's abort
+// flag and bit 2 of the model's device error word.  Both CTAs meet at a
+// cluster barrier before leaving, and the chains are written back only when
+// neither CTA aborted.
+#include "bm_internal.cuh"
+#include "tc_common.cuh"
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+
+using namespace bmtc;
+
+namespace {
+
+constexpr int kNA = 3;                  // coupling ring slots
+constexpr int kNB = 2;                  // one-hot ring slots (NC x 128 bytes each)
+constexpr int kKC = 64;                 // fp16 K elements per chunk (128-byte rows)
+constexpr int kRowsA = 128;             // MMA M
+constexpr int kTileA = kRowsA * 128;    // one hi or lo tile (16 KB)
+constexpr int kSlotA = 2 * kTileA;      // ring slot: hi tile, then lo tile
+constexpr int kQmax = 32;
+constexpr int kBmax = 32;
+constexpr int kDrawWarps = 5, kGenWarps = 5;
+constexpr int kDraw = 32 * kDrawWarps;  // drawer threads
+constexpr int kGen = 32 * kGenWarps;    // generator threads
+constexpr int kThreads = 64 + kDraw + kGen;
+constexpr int kNCmax = 160;
+constexpr int kNBars = 2 * kNA + 2 * kNB + 2 + 2 + 2 + 1 + 1;
+
+// ---------------------------------------------------------------- cluster helpers
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster_u8(uint32_t a, unsigned short v)
+{
+    asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(a), "h"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void mbar_arrive_peer(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_cl(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait with acquire semantics at cluster scope (barriers that the
+// peer CTA arrives on, or whose arrivals follow data the peer wrote).
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
+{
+    if (mbar_try_cl(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (;;) {
+        if (mbar_try_cl(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicOr(err, 4);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- tcgen05 helpers
+// K-major no-swizzle descriptor: K-adjacent core matrices 128 bytes apart,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_noswz(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+// Byte offset of 16-byte piece p of row r in a no-swizzle K-major tile with
+// 8 pieces per row.
+__device__ __forceinline__ uint32_t noswz_off(int r, int p)
+{
+    return (uint32_t)((((r >> 3) << 3) + p) << 7) + (uint32_t)((r & 7) << 4);
+}
+
+struct PairArgs {
+    const float *h;
+    const float *Jc;  // in-block coupling blocks: [site block][pair slot][b][a padded to q4]
+    uint8_t *states;
+    int *err;
+    uint64_t seed, sweep0, chain0;
+    float beta_l2e;   // beta * log2(e): weights exp(beta H) = 2^(beta log2(e) H)
+    int M, L, q, Lp, B, nb, nK, X, NC;
+    long long nblocks;
+    uint32_t tmem_cols, acc_stride;
+};
+
+__host__ __device__ inline int st_stride(int Lp) { return Lp + 4; }
+__host__ __device__ inline int snap_stride(int B) { return 4 * (((B + 3) / 4) | 1); }
+__host__ __device__ inline int q4_of(int q) { return (q + 3) & ~3; }
+// Row stride (floats) of the staged fields, one row per chain: q rounded up
+// to 4, plus 4 when that is an even number of 16-byte units, so that eight
+// consecutive rows start in eight different 16-byte bank groups.
+__host__ __device__ inline int hs_stride(int q) { return ((q4_of(q) >> 2) & 1) ? q4_of(q) : q4_of(q) + 4; }
+__host__ __device__ inline int corr_slots(int B) { return B * (B - 1) / 2; }
+
+struct Smem {
+    uint32_t a, b, hs, st, snap, corr, hrow, jtab, bars, misc, total;
+};
+
+__host__ __device__ inline Smem smem_layout(int NC, int Lp, int B, int nK, int q)
+{
+    Smem s;
+    s.a = 0;
+    s.b = s.a + kNA * kSlotA;
+    s.hs = s.b + kNB * NC * 128;
+    s.st = s.hs + NC * hs_stride(q) * 4;          // fields h + G of one site: [chain][a]
+    s.snap = s.st + NC * st_stride(Lp);           // [2 pair slots][2 blocks][NC][snap_stride]
+    s.corr = (s.snap + 4 * NC * snap_stride(B) + 15) & ~15u;
+    s.hrow = s.corr + (uint32_t)corr_slots(B) * q * q4_of(q) * 4;
+    s.jtab = s.hrow + kRowsA * 4;
+    s.bars = (s.jtab + nK * 4 + 15) & ~15u;
+    s.misc = s.bars + kNBars * 8;
+    s.total = s.misc + 16;
+    return s;
+}
+
+struct Blk {
+    int i0, Bk;
+};
+
+__device__ __forceinline__ Blk blk_of(const PairArgs &p, long long kb)
+{
+    Blk g;
+    g.i0 = (int)(kb % p.nb) * p.B;
+    g.Bk = min(p.B, p.L - g.i0);
+    return g;
+}
+
+__device__ __forceinline__ void blk_chunks(const PairArgs &p, long long kb, int &lo, int &hi)
+{
+    const Blk g = blk_of(p, kb);
+    lo = g.i0 * p.q / kKC;
+    hi = ((g.i0 + g.Bk) * p.q - 1) / kKC;
+}
+
+// One step of pair P's schedule in CTA r: n K chunks (n0 from c0, the rest
+// from c1), main or delta, the own block t they feed, the block whose
+// accumulator is complete after the step, the blocks a delta step carries,
+// and what the generator waits for first (kind 1: the ready barrier of
+// block wait_kb; kind 2: CTA 0's snapshot barrier after block wait_kb).
+struct Seg {
+    int n, n0, c0, c1, wait_kind;
+    bool delta;
+    long long t, wait_kb, commit_kb, d0, d1;
+};
+
+__device__ __forceinline__ int seg_chunk(const Seg &s, int k) { return k < s.n0 ? s.c0 + k : s.c1 + (k - s.n0); }
+
+__device__ Seg seg_info(const PairArgs &p, long long P, int step, int r)
+{
+    Seg s;
+    s.n = s.n0 = s.c0 = s.c1 = s.wait_kind = 0;
+    s.delta = false;
+    s.t = s.wait_kb = s.commit_kb = s.d0 = s.d1 = -1;
+    const long long own = 2 * P + r;
+    const bool has = own < p.nblocks;
+    if (step == 0 || step == 2) {
+        if (!has) return s;
+        s.c0 = step == 0 ? 0 : p.X;
+        s.n = s.n0 = step == 0 ? p.X : p.nK - p.X;
+        s.t = own;
+        if (step == 2 && P == 0 && r == 0) s.commit_kb = 0;
+        return s;
+    }
+    if (P < 1) return s;
+    s.delta = true;
+    if (step == 1) {
+        if (r != 1 || 2 * P - 1 >= p.nblocks) return s;
+        int lo, hi;
+        blk_chunks(p, 2 * P - 2, lo, hi);
+        s.c0 = lo;
+        s.n = s.n0 = hi - lo + 1;
+        s.t = 2 * P - 1;
+        s.d0 = 2 * P - 2;
+        s.wait_kb = 2 * P - 2;
+        s.wait_kind = 1;
+        s.commit_kb = 2 * P - 1;
+        return s;
+    }
+    if (!has) return s;
+    int a0, a1, c0, c1;
+    blk_chunks(p, 2 * P - 2, a0, a1);
+    blk_chunks(p, 2 * P - 1, c0, c1);
+    if (c0 <= a1 + 1 && a0 <= c1 + 1) {
+        s.c0 = min(a0, c0);
+        s.n = s.n0 = max(a1, c1) - s.c0 + 1;
+    } else {  // the two blocks wrap around the end of a sweep
+        s.c0 = a0;
+        s.n0 = a1 - a0 + 1;
+        s.c1 = c0;
+        s.n = s.n0 + (c1 - c0 + 1);
+    }
+    s.t = own;
+    s.d0 = 2 * P - 2;
+    s.d1 = 2 * P - 1;
+    s.wait_kb = 2 * P - 1;
+    s.wait_kind = r == 0 ? 2 : 1;
+    s.commit_kb = r == 0 ? own : -1;
+    return s;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    k_gibbs_pair(const __grid_constant__ CUtensorMap tm_jp, const PairArgs p)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    const Smem lay = smem_layout(p.NC, p.Lp, p.B, p.nK, p.q);
+    float *Hs = reinterpret_cast<float *>(base + lay.hs);
+    uint8_t *st = base + lay.st;
+    uint8_t *snap = base + lay.snap;
+    const float4 *corr4 = reinterpret_cast<const float4 *>(base + lay.corr);
+    float *hrow = reinterpret_cast<float *>(base + lay.hrow);
+    unsigned short *jtab = reinterpret_cast<unsigned short *>(base + lay.jtab);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + lay.bars);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + lay.misc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(base + lay.misc + 4);
+    const uint32_t full_a = su32(bars), empty_a = full_a + 8 * kNA;
+    const uint32_t full_b = empty_a + 8 * kNA, empty_b = full_b + 8 * kNB;
+    const uint32_t acc_full = empty_b + 8 * kNB;  // [2], own block j = kb/2 in slot j % 2
+    const uint32_t acc_empty = acc_full + 16;     // [2]
+    const uint32_t ready = acc_empty + 16;        // [2], states after block kb: barrier kb % 2
+    const uint32_t snapready = ready + 16;        // CTA 0: next pair's snapshots taken
+    const uint32_t corr_bar = snapready + 8;      // staged coupling blocks of the own block
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = (int)cluster_rank(), peer = r ^ 1;
+    const int q = p.q, L = p.L, NC = p.NC, Lp = p.Lp;
+    const int Sst = st_stride(Lp), Ssn = snap_stride(p.B);
+    const size_t cta0 = (size_t)(blockIdx.x >> 1) * NC;
+    const long long nblocks = p.nblocks;
+    const long long npairs = (nblocks + 1) / 2;
+    auto snap_of = [&](long long kb) { return snap + (size_t)((((kb >> 1) & 1) * 2 + (kb & 1)) * NC) * Ssn; };
+
+    if (tid == 0) {
+        for (int s = 0; s < kNA; ++s) {
+            mbar_init(full_a + 8 * s, 1);
+            mbar_init(empty_a + 8 * s, 1);
+        }
+        for (int s = 0; s < kNB; ++s) {
+            mbar_init(full_b + 8 * s, kGenWarps);
+            mbar_init(empty_b + 8 * s, 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(acc_full + 8 * s, 1);
+            mbar_init(acc_empty + 8 * s, kDrawWarps);
+            mbar_init(ready + 8 * s, kDraw);
+        }
+        mbar_init(snapready, kDraw);
+        mbar_init(corr_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int k = tid; k < NC * Lp; k += kThreads) {
+        const int c = k / Lp, x = k - c * Lp;
+        const size_t m = cta0 + c;
+        st[c * Sst + x] = (m < (size_t)p.M && x < L) ? p.states[m * L + x] : 0;
+    }
+    for (int c = tid; c < p.nK; c += kThreads) {
+        const int k0 = c * kKC;
+        jtab[2 * c] = (unsigned short)min(L - 1, k0 / q);
+        jtab[2 * c + 1] = (unsigned short)min(L - 1, (k0 + kKC - 1) / q);
+    }
+    __syncthreads();
+    for (long long kb = 0; kb < 2 && kb < nblocks; ++kb) {  // snapshots of pair 0
+        const Blk g = blk_of(p, kb);
+        uint8_t *sn = snap_of(kb);
+        for (int k = tid; k < NC * g.Bk; k += kThreads) {
+            const int c = k / g.Bk, x = k - c * g.Bk;
+            sn[c * Ssn + x] = st[c * Sst + g.i0 + x];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    cluster_sync_all();  // both CTAs' barriers are initialised before any remote arrival
+    const uint32_t tmem = *tmem_slot;
+
+    // Stage the in-block coupling blocks of block kb (its pairs pi > pj are
+    // the first Bk(Bk-1)/2 slots of its Jc entry): one bulk copy.
+    auto stage_corr = [&](long long kb) {
+        const Blk g = blk_of(p, kb);
+        const uint32_t row = (uint32_t)q * (uint32_t)q4_of(q);
+        const uint32_t bytes = (uint32_t)corr_slots(g.Bk) * row * 4u;
+        mbar_expect_tx(corr_bar, bytes);
+        if (bytes > 0)
+            bulk_g2s(su32(base + lay.corr), p.Jc + (size_t)(kb % p.nb) * corr_slots(p.B) * row, bytes, corr_bar);
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            long long issued = 0;
+            int sa = 0, lap = 0;
+            bool ok = true;
+            for (long long P = 0; P <= npairs && ok; ++P)
+                for (int step = 0; step < 4 && ok; ++step) {
+                    const Seg sg = seg_info(p, P, step, r);
+                    const int r0 = sg.n > 0 ? (int)(sg.t % p.nb) * kRowsA : 0;
+                    for (int k = 0; k < sg.n && ok; ++k) {
+                        const int c = seg_chunk(sg, k);
+                        if (lap > 0 && !mbar_wait(empty_a + 8 * sa, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t dst = su32(base + lay.a + sa * kSlotA), bar = full_a + 8 * sa;
+                        mbar_expect_tx(bar, (uint32_t)kSlotA);
+                        tma_load_3d(dst, &tm_jp, 0, r0, 2 * c, bar);  // hi slab then lo slab of 128 rows
+                        ++issued;
+                        if (++sa == kNA) {
+                            sa = 0;
+                            ++lap;
+                        }
+                    }
+                }
+            if (*abort_flag) {
+                volatile int no_abort = 0;
+                for (long long u = issued > kNA ? issued - kNA : 0; u < issued; ++u)
+                    mbar_wait(full_a + 8 * (int)(u % kNA), (uint32_t)((u / kNA) & 1), &no_abort, p.err);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            // kind::f16: D F32 (bit 4), A = B = F16, K-major, N >> 3 at 17, M >> 4 at 24.
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kRowsA >> 4) << 24);
+            int sa = 0, sb = 0;
+            uint32_t pha = 0, phb = 0;
+            bool ok = true;
+            for (long long P = 0; P <= npairs && ok; ++P)
+                for (int step = 0; step < 4 && ok; ++step) {
+                    const Seg sg = seg_info(p, P, step, r);
+                    const long long j = sg.t >> 1;  // own block index
+                    for (int k = 0; k < sg.n && ok; ++k) {
+                        const int c = seg_chunk(sg, k);
+                        const bool first = !sg.delta && c == 0;
+                        if (!mbar_wait(full_b + 8 * sb, phb, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        if (!mbar_wait(full_a + 8 * sa, pha, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        if (first && j >= 2 &&
+                            !mbar_wait(acc_empty + 8 * (int)(j & 1), (uint32_t)(((j - 2) >> 1) & 1), abort_flag,
+                                       p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t bb = su32(base + lay.b + sb * NC * 128);
+                        const uint32_t ah = su32(base + lay.a + sa * kSlotA), al = ah + kTileA;
+                        const uint32_t dcol = tmem + (uint32_t)(j & 1) * p.acc_stride;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t bd = desc_noswz(bb + kk * 256);
+                            mma_f16(dcol, desc_sw128(ah + kk * 32), bd, idesc, (first && kk == 0) ? 0u : 1u);
+                            mma_f16(dcol, desc_sw128(al + kk * 32), bd, idesc, 1u);
+                        }
+                        mma_commit(empty_a + 8 * sa);
+                        if (++sa == kNA) {
+                            sa = 0;
+                            pha ^= 1u;
+                        }
+                        mma_commit(empty_b + 8 * sb);
+                        if (++sb == kNB) {
+                            sb = 0;
+                            phb ^= 1u;
+                        }
+                    }
+                    if (ok && sg.commit_kb >= 0) mma_commit(acc_full + 8 * (int)((sg.commit_kb >> 1) & 1));
+                }
+        }
+    } else if (warp < 2 + kDrawWarps) {
+        // ------------------------------------------------------------ drawers (warps 2-6)
+        // Uniform control flow: every drawer runs the whole loop nest and meets
+        // every named barrier; after an abort the work is skipped.
+        const int w = tid - 64;                 // 0..kDraw-1, chain w
+        const bool tm_reader = warp < 6;        // warps 2-5 cover TMEM lane quarters 2, 3, 0, 1
+        const int lane_base = 32 * (warp & 3);
+        const int row = lane_base + lane;
+        const int HS = hs_stride(q), qv = q4_of(q) >> 2;  // float4s per padded row
+        const uint32_t st_peer = peer_addr(su32(st), (uint32_t)peer);
+        const uint32_t ready_peer = peer_addr(ready, (uint32_t)peer);
+        bool ok = true;
+        long long staged = 0;
+        if (w == 0 && r < nblocks) {
+            stage_corr(r);
+            staged = 1;
+        }
+        for (long long kb = r; kb < nblocks; kb += 2) {
+            const long long j = kb >> 1;
+            const Blk g = blk_of(p, kb);
+            const int slot = (int)(j & 1);
+            const uint64_t sweep = p.sweep0 + (uint64_t)(kb / p.nb);
+            if (ok && !mbar_wait(acc_full + 8 * slot, (uint32_t)((j >> 1) & 1), abort_flag, p.err)) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int k = w; k < g.Bk * q; k += kDraw) hrow[k] = p.h[(size_t)g.i0 * q + k];
+            if (ok && !mbar_wait(corr_bar, (uint32_t)(j & 1), abort_flag, p.err)) ok = false;
+            ok = !named_bar_or(1, kDraw, !ok || *abort_flag);
+            const uint8_t *old = snap_of(kb);
+            const uint32_t tacc = tmem + ((uint32_t)lane_base << 16) + (uint32_t)slot * p.acc_stride;
+            for (int pp = 0; pp < g.Bk && ok; ++pp) {
+                const int r0 = pp * q;
+                if (tm_reader && lane_base < r0 + q && lane_base + 32 > r0) {
+                    const bool mine = row >= r0 && row < r0 + q;
+                    const float hv = mine ? hrow[row] : 0.0f;
+                    for (int c0 = 0; c0 < NC; c0 += 16) {
+                        uint32_t v[16];
+                        tmem_ld16(tacc + (uint32_t)c0, v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (mine) {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) Hs[(c0 + e) * HS + (row - r0)] = hv + __uint_as_float(v[e]);
+                        }
+                    }
+                }
+                named_bar_sync(1, kDraw);
+                const int i = g.i0 + pp;
+                if (w < NC) {
+                    const int ch = w;
+                    const uint64_t m = p.chain0 + cta0 + ch;
+                    // the uniform first: it does not depend on the states
+                    const uint32_t r24 = bm_u24(p.seed, m, sweep, (uint64_t)i, 0);
+                    float H[32];
+                    const float4 *hs4 = reinterpret_cast<const float4 *>(Hs + ch * HS);
+#pragma unroll
+                    for (int a4 = 0; a4 < 8; ++a4)
+                        if (a4 < qv) {
+                            const float4 t = hs4[a4];
+                            H[4 * a4] = t.x;
+                            H[4 * a4 + 1] = t.y;
+                            H[4 * a4 + 2] = t.z;
+                            H[4 * a4 + 3] = t.w;
+                        }
+                    // sites jj < pp of the block redrawn since the MMAs: + J_ij(., new) - J_ij(., old)
+                    const float4 *cb = corr4 + (size_t)(pp * (pp - 1) / 2) * q * qv;
+                    for (int jj = 0; jj < pp; ++jj) {
+                        const int sn = st[ch * Sst + g.i0 + jj], so = old[ch * Ssn + jj];
+                        if (sn == so) continue;
+                        const float4 *rn = cb + (jj * q + sn) * qv, *ro = cb + (jj * q + so) * qv;
+#pragma unroll
+                        for (int a4 = 0; a4 < 8; ++a4)
+                            if (a4 < qv) {
+                                const float4 vn = rn[a4], vo = ro[a4];
+                                H[4 * a4] += vn.x - vo.x;
+                                H[4 * a4 + 1] += vn.y - vo.y;
+                                H[4 * a4 + 2] += vn.z - vo.z;
+                                H[4 * a4 + 3] += vn.w - vo.w;
+                            }
+                    }
+                    float mx = -INFINITY;
+#pragma unroll
+                    for (int a = 0; a < 32; ++a)
+                        if (a < q) {
+                            H[a] *= p.beta_l2e;
+                            mx = fmaxf(mx, H[a]);
+                        }
+                    float S = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < 32; ++a)
+                        if (a < q) {
+                            S += exp2f(H[a] - mx);
+                            H[a] = S;  // prefix sums of exp(beta H_a - max_b beta H_b)
+                        }
+                    const float thr = ((float)r24 * 5.9604644775390625e-8f) * S;
+                    int pick = q - 1;
+#pragma unroll
+                    for (int a = 31; a >= 0; --a)
+                        if (a < q && thr < H[a]) pick = a;
+                    st[ch * Sst + i] = (uint8_t)pick;
+                    st_cluster_u8(st_peer + (uint32_t)(ch * Sst + i), (unsigned short)pick);
+                }
+                named_bar_sync(1, kDraw);  // Hs is rewritten for the next site
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + 8 * slot);
+            named_bar_sync(1, kDraw);  // the staged coupling blocks are free again
+            if (w == 0 && ok && !*abort_flag && kb + 2 < nblocks) {
+                stage_corr(kb + 2);
+                ++staged;
+            }
+            // CTA 1: the next pair's snapshots, before block kb is published
+            // (CTA 0 starts rewriting block kb+1's sites once it has it).
+            if (r == 1 && kb + 1 < nblocks) {
+                if (ok && !mbar_wait_cl(ready + 8 * (int)((kb - 1) & 1), (uint32_t)(((kb - 1) >> 1) & 1), abort_flag,
+                                        p.err))
+                    ok = false;
+                if (ok && w < NC)
+                    for (long long nb2 = kb + 1; nb2 <= kb + 2 && nb2 < nblocks; ++nb2) {
+                        const Blk gn = blk_of(p, nb2);
+                        uint8_t *sn = snap_of(nb2) + w * Ssn;
+                        for (int x = 0; x < gn.Bk; ++x) sn[x] = st[w * Sst + gn.i0 + x];
+                    }
+            }
+            // publish block kb: own generator and the peer
+            mbar_arrive(ready + 8 * (int)(kb & 1));
+            mbar_arrive_peer(ready_peer + 8 * (uint32_t)(kb & 1));
+            // CTA 0: the next pair's snapshots once block kb+1 has arrived
+            if (r == 0 && kb + 1 < nblocks) {
+                if (ok && !mbar_wait_cl(ready + 8 * (int)((kb + 1) & 1), (uint32_t)(((kb + 1) >> 1) & 1), abort_flag,
+                                        p.err))
+                    ok = false;
+                if (ok && w < NC)
+                    for (long long nb2 = kb + 2; nb2 <= kb + 3 && nb2 < nblocks; ++nb2) {
+                        const Blk gn = blk_of(p, nb2);
+                        uint8_t *sn = snap_of(nb2) + w * Ssn;
+                        for (int x = 0; x < gn.Bk; ++x) sn[x] = st[w * Sst + gn.i0 + x];
+                    }
+                mbar_arrive(snapready);
+            }
+        }
+        if (!ok) *abort_flag = 1;
+        if (w == 0 && *abort_flag && staged > 0) {
+            volatile int no_abort = 0;
+            mbar_wait(corr_bar, (uint32_t)((staged - 1) & 1), &no_abort, p.err);
+        }
+    } else {
+        // ------------------------------------------------------------ generators (warps 7-11)
+        const int w = tid - 64 - kDraw;  // 0..kGen-1, operand row of chain w
+        const bool own = w < NC;
+        unsigned char *const row0 = base + lay.b + noswz_off(own ? w : 0, 0);
+        const uint8_t *const strow = st + (own ? w : 0) * Sst;
+        const int wrow = (own ? w : 0) * Ssn;
+        int sb = 0, lap = 0;
+        bool ok = true;
+        for (long long P = 0; P <= npairs && ok; ++P) {
+            int s0lo = L, s0hi = L, s1lo = L, s1hi = L;
+            const uint8_t *ps0 = snap, *ps1 = snap;
+            if (P >= 1) {
+                const Blk g0 = blk_of(p, 2 * P - 2), g1 = blk_of(p, 2 * P - 1);
+                s0lo = g0.i0;
+                s0hi = g0.i0 + g0.Bk;
+                s1lo = g1.i0;
+                s1hi = g1.i0 + g1.Bk;
+                ps0 = snap_of(2 * P - 2) + wrow;
+                ps1 = snap_of(2 * P - 1) + wrow;
+            }
+            for (int step = 0; step < 4 && ok; ++step) {
+                const Seg sg = seg_info(p, P, step, r);
+                if (sg.n > 0 && sg.wait_kind != 0) {
+                    const uint32_t bar = sg.wait_kind == 1 ? ready + 8 * (uint32_t)(sg.wait_kb & 1) : snapready;
+                    if (!mbar_wait_cl(bar, (uint32_t)((sg.wait_kb >> 1) & 1), abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                for (int k = 0; k < sg.n; ++k) {
+                    if (lap > 0 && !mbar_wait(empty_b + 8 * sb, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    const int c = seg_chunk(sg, k);
+                    const int k0 = c * kKC;
+                    unsigned char *rowp = row0 + sb * NC * 128;
+                    if (own) {
+#pragma unroll
+                        for (int pc = 0; pc < 8; ++pc)
+                            *reinterpret_cast<uint4 *>(rowp + pc * 128) = make_uint4(0, 0, 0, 0);
+                        if (!sg.delta) {
+                            const int jlo = jtab[2 * c], jhi = jtab[2 * c + 1];
+                            for (int jj = jlo; jj <= jhi; ++jj) {
+                                const int sj = (jj >= s0lo && jj < s0hi)   ? ps0[jj - s0lo]
+                                               : (jj >= s1lo && jj < s1hi) ? ps1[jj - s1lo]
+                                                                           : strow[jj];
+                                const int pos = jj * q + sj - k0;
+                                if (pos >= 0 && pos < kKC)
+                                    *reinterpret_cast<unsigned short *>(rowp + (pos >> 3) * 128 + (pos & 7) * 2) =
+                                        0x3c00u;
+                            }
+                        } else {
+                            for (int u = 0; u < 2; ++u) {
+                                const long long db = u == 0 ? sg.d0 : sg.d1;
+                                if (db < 0) continue;
+                                const Blk gd = blk_of(p, db);
+                                const uint8_t *po = (u == 0 ? ps0 : ps1);  // d0 = 2P-2, d1 = 2P-1
+                                for (int x = 0; x < gd.Bk; ++x) {
+                                    const int jj = gd.i0 + x;
+                                    const int sn = strow[jj], so = po[x];
+                                    if (sn == so) continue;
+                                    const int pn = jj * q + sn - k0, pd = jj * q + so - k0;
+                                    if (pn >= 0 && pn < kKC)
+                                        *reinterpret_cast<unsigned short *>(rowp + (pn >> 3) * 128 + (pn & 7) * 2) =
+                                            0x3c00u;
+                                    if (pd >= 0 && pd < kKC)
+                                        *reinterpret_cast<unsigned short *>(rowp + (pd >> 3) * 128 + (pd & 7) * 2) =
+                                            0xbc00u;
+                                }
+                            }
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(full_b + 8 * sb);
+                    if (++sb == kNB) {
+                        sb = 0;
+                        ++lap;
+                    }
+                }
+            }
+        }
+        if (!ok) *abort_flag = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols)
+                     : "memory");
+    // No remote store or arrival into either CTA is in flight past this
+    // barrier; then each CTA reads the other's abort flag, and the second
+    // barrier keeps both CTAs resident until those reads are done.
+    cluster_sync_all();
+    const bool bad = *abort_flag != 0 || ld_cluster_u32(peer_addr(su32((const void *)abort_flag), (uint32_t)peer)) != 0;
+    cluster_sync_all();
+    if (bad) return;
+    const int half = NC / 2;  // CTA r writes back chains 2c + r
+    for (int k = tid; k < half * L; k += kThreads) {
+        const int cc = k / L, x = k - cc * L;
+        const int c = 2 * cc + r;
+        const size_t m = cta0 + c;
+        if (m < (size_t)p.M) p.states[m * L + x] = st[c * Sst + x];
+    }
+}
+
+// Jc[blk][slot][b][a4] = J_ij(a, b) for i = blk*B + pi, j = blk*B + pj,
+// slot = pi*(pi-1)/2 + pj (pi > pj); zero for a >= q or i >= L.
+__global__ void k_build_corr(const float *__restrict__ J, float *__restrict__ Jc, int L, int q, int B, int nb)
+{
+    const int q4 = q4_of(q), slots = corr_slots(B);
+    const size_t n = (size_t)nb * slots * q * q4;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t % q4);
+        size_t u = t / q4;
+        const int b = (int)(u % q);
+        u /= q;
+        const int slot = (int)(u % slots), blk = (int)(u / slots);
+        int pi = 1;
+        while ((pi + 1) * pi / 2 <= slot) ++pi;
+        const int pj = slot - pi * (pi - 1) / 2;
+        const int i = blk * B + pi, j = blk * B + pj;
+        Jc[t] = (a < q && i < L) ? J[(((size_t)i * L + j) * q + a) * q + b] : 0.0f;
+    }
+}
+
+int corr_prepare(bm_model_s *m, int B, cudaStream_t st)
+{
+    if (m->corr_current) return BM_OK;
+    const int nb = (m->L + B - 1) / B;
+    const size_t n = (size_t)nb * corr_slots(B) * m->q * q4_of(m->q);
+    if (!m->Jc) BM_CK(cudaMalloc(&m->Jc, std::max<size_t>(n, 4) * sizeof(float)));
+    if (n > 0) {
+        const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+        k_build_corr<<<grid, 256, 0, st>>>(m->J, m->Jc, m->L, m->q, B, nb);
+        BM_CK_LAUNCH("k_build_corr");
+    }
+    m->corr_current = true;
+    return BM_OK;
+}
+
+int g_max_clusters[64];
+std::once_flag g_clusters_once[64];
+
+// Clusters of two one-CTA-per-SM CTAs that the device runs at once.
+int max_clusters(const bm_model_s *m)
+{
+    const int dev = m->device >= 0 && m->device < 64 ? m->device : 0;
+    std::call_once(g_clusters_once[dev], [&] {
+        int n = (m->num_sms > 0 ? m->num_sms : 2) / 2;
+        const int smem = 200 * 1024;  // any size above half an SM's shared memory: one CTA per SM
+        if (cudaFuncSetAttribute(k_gibbs_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(2, 1, 1);
+            cfg.blockDim = dim3(kThreads, 1, 1);
+            cfg.dynamicSmemBytes = smem;
+            int c = 0;  // the kernel's cluster shape (2 CTAs) is fixed at compile time
+            if (cudaOccupancyMaxActiveClusters(&c, k_gibbs_pair, &cfg) == cudaSuccess && c > 0) n = c;
+        }
+        (void)cudaGetLastError();
+        g_max_clusters[dev] = n > 0 ? n : 1;
+    });
+    return g_max_clusters[dev];
+}
+
+}  // namespace
+
+// Chains per cluster for the two-CTA tensor-core sweep (multiple of 16,
+// <= 160), or 0 when the shape does not fit one CTA's shared memory or L < 2.
+int bm_gibbs_pair_chains_per_cluster(const bm_model_s *m, int M)
+{
+    if (m->L < 2 || m->L > 65535 || m->q > kQmax) return 0;
+    const int B = bm_split_block_sites(m->L, m->q);
+    if (B > kBmax) return 0;
+    const int ncl = max_clusters(m);
+    int nc = (M + ncl - 1) / ncl;
+    nc = std::max(16, (nc + 15) & ~15);
+    nc = std::min(nc, kNCmax);
+    const int Lp = (m->L + 15) & ~15;
+    const int nK = (m->L * m->q + kKC - 1) / kKC;
+    while (nc >= 16 && smem_layout(nc, Lp, B, nK, m->q).total + 1024 > 227 * 1024) nc -= 16;
+    return nc >= 16 ? nc : 0;
+}
+
+// Waves of clusters the two-CTA sweep of M chains needs (0: does not fit).
+int bm_gibbs_pair_waves(const bm_model_s *m, int M)
+{
+    const int nc = bm_gibbs_pair_chains_per_cluster(m, M);
+    if (nc == 0) return 0;
+    const int ncl = max_clusters(m);
+    return ((M + nc - 1) / nc + ncl - 1) / ncl;
+}
+
+int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)
+{
+    const int NC = bm_gibbs_pair_chains_per_cluster(m, c->M);
+    if (NC == 0) return bm_fail(BM_EINVAL, "two-CTA tensor-core sweep: shape does not fit shared memory");
+    {
+        int rc = bm_split_prepare(m, 0, st);
+        if (rc == BM_OK) rc = corr_prepare(m, bm_split_block_sites(c->L, c->q), st);
+        if (rc != BM_OK) return rc;
+    }
+    PairArgs a;
+    a.h = m->h;
+    a.Jc = m->Jc;
+    a.states = c->s;
+    a.err = m->dflags + 3;
+    a.seed = c->seed;
+    a.sweep0 = c->sweep;
+    a.chain0 = c->chain0;
+    a.beta_l2e = (float)((double)beta * 1.4426950408889634);
+    a.M = c->M;
+    a.L = c->L;
+    a.q = c->q;
+    a.Lp = (c->L + 15) & ~15;
+    a.B = bm_split_block_sites(c->L, c->q);
+    a.nb = (c->L + a.B - 1) / a.B;
+    a.nK = m->Kp / kKC;
+    a.NC = NC;
+    a.nblocks = (long long)nsweeps * a.nb;
+    a.X = a.nK / 2;
+    a.acc_stride = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;
+    a.tmem_cols = 2 * a.acc_stride;
+    const Smem lay = smem_layout(NC, a.Lp, a.B, a.nK, a.q);
+    const size_t smem = lay.total + 1024;
+    BM_CK(cudaFuncSetAttribute(k_gibbs_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nclusters = (c->M + NC - 1) / NC;
+    k_gibbs_pair<<<2 * nclusters, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(m->tmap_jp), a);
+    BM_CK_LAUNCH("k_gibbs_pair");
+    return BM_OK;
+}

@@ -259,8 +259,10 @@ int bm_server_add_model(bm_server s, bm_model m, int *id)
     cudaStream_t st = nullptr;
     BM_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     int rc = BM_OK;
-    const bool mma = m->engine == BM_ENGINE_MMA || (m->engine == BM_ENGINE_AUTO && m->q >= 10);
-    if (mma && bm_gibbs_mma_chains_per_cta(m, 1) > 0) rc = bm_split_prepare(m, 0, st);
+    const bool mma = m->engine == BM_ENGINE_MMA || m->engine == BM_ENGINE_MMA_PAIR ||
+                     (m->engine == BM_ENGINE_AUTO && m->q >= 10);
+    if (mma && (bm_gibbs_mma_chains_per_cta(m, 1) > 0 || bm_gibbs_pair_chains_per_cluster(m, 1) > 0))
+        rc = bm_split_prepare(m, 0, st);
     const cudaError_t e = cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     if (rc != BM_OK) return rc;

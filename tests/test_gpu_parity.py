@@ -29,13 +29,14 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-GIBBS_ENGINES = ["simt", "mma"]
+GIBBS_ENGINES = ["simt", "mma", "mma_pair"]
 
 
 def load(bm, h, J, engine=None):
     m = bm.bm_potts_load(to_dev(h), to_dev(J))
     if engine is not None:
-        bm.bm_model_set_engine(m, {"simt": bm.BM_ENGINE_SIMT, "mma": bm.BM_ENGINE_MMA}[engine])
+        bm.bm_model_set_engine(m, {"simt": bm.BM_ENGINE_SIMT, "mma": bm.BM_ENGINE_MMA,
+                                   "mma_pair": bm.BM_ENGINE_MMA_PAIR}[engine])
     return m
 
 
@@ -165,11 +166,36 @@ def test_gibbs_config2_launch_sampled_chains(bm, orc, engine):
     bm.bm_device_status(m)
     s1 = states_of(bm, c)
     rng = np.random.default_rng(0)
-    sample = sorted(set(rng.choice(M, 24, replace=False).tolist()) | {0, 65, 66, 79, 80, M - 1})
+    # CTA / cluster boundaries of the tensor-core forms (80 and 144 chains) and the tail
+    sample = sorted(set(rng.choice(M, 24, replace=False).tolist()) | {0, 65, 66, 79, 80, 143, 144, M - 1})
     h64, J64 = h.astype(np.float64), J.astype(np.float64)
     for k in sample:
         bad, worst, _ = orc.gibbs_verify(h64, J64, s0[k:k + 1], s1[k:k + 1], 2024, 0, 1.0, k)
         assert bad == 0 or worst < FLIP_MARGIN, (k, bad, worst)
+
+
+@pytest.mark.parametrize("engine", ["mma", "mma_pair"])
+def test_gibbs_more_chains_than_one_wave(bm, orc, engine):
+    """M = 12000 chains: more CTAs (clusters) than the GPU runs at once, so
+    later ones start when earlier ones finish; two sweeps, sampled chains of
+    every part of the launch verified."""
+    L, q, M = 24, 21, 12000
+    h, J = synth.planted_local_model(L, q, 12, sigma_h=1.0, sigma_J=0.3)
+    m = load(bm, h, J, engine)
+    c = bm.bm_chains_init(m, M, 77)
+    s0 = states_of(bm, c)
+    bm.bm_gibbs_sweep(m, c, 1, 1.0)
+    s1 = states_of(bm, c)
+    bm.bm_gibbs_sweep(m, c, 1, 1.0)
+    bm.bm_device_status(m)
+    s2 = states_of(bm, c)
+    rng = np.random.default_rng(1)
+    sample = sorted(set(rng.choice(M, 40, replace=False).tolist()) | {0, 159, 160, 11519, 11520, M - 1})
+    h64, J64 = h.astype(np.float64), J.astype(np.float64)
+    for k in sample:
+        for sw, (a, b) in enumerate([(s0, s1), (s1, s2)]):
+            bad, worst, _ = orc.gibbs_verify(h64, J64, a[k:k + 1], b[k:k + 1], 77, sw, 1.0, k)
+            assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
 
 
 def test_gibbs_rejects_bad_arguments(bm):
@@ -498,3 +524,20 @@ def test_shards_reproduce_the_full_ensemble(bm, engine):
     bm.bm_chain_stats(full, ref)
     torch.cuda.synchronize()
     assert torch.equal(tot, ref)
+
+
+def test_sweep_engine_resolution(bm):
+    """AUTO resolves to the two-CTA tensor-core form for protein alphabets and
+    to the CUDA-core form for small alphabets; explicit engines are kept."""
+    h, J = synth.planted_local_model(64, 21, 3)
+    m = load(bm, h, J)
+    assert bm.bm_model_sweep_engine(m, 10000) == bm.BM_ENGINE_MMA_PAIR
+    assert bm.bm_model_sweep_engine(m, 1) == bm.BM_ENGINE_MMA_PAIR
+    bm.bm_model_set_engine(m, bm.BM_ENGINE_MMA)
+    assert bm.bm_model_sweep_engine(m, 10000) == bm.BM_ENGINE_MMA
+    h5, J5 = synth.planted_local_model(64, 5, 3)
+    m5 = load(bm, h5, J5)
+    assert bm.bm_model_sweep_engine(m5, 10000) == bm.BM_ENGINE_SIMT
+    with pytest.raises(bm.BmError) as e:
+        bm.bm_model_sweep_engine(m5, 0)
+    assert e.value.code == bm.BM_EINVAL

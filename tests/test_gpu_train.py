@@ -29,7 +29,7 @@ DEV = "cuda"
 L, Q, N = 16, 5, 20000
 LR = 0.5
 TRACK_M, TRACK_ITERS = 4096, 40
-ENGINES = ["simt", "mma"]
+ENGINES = ["simt", "mma", "mma_pair"]
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +67,8 @@ def gpu_train(bm, data, engine, M, max_iters, target):
     stats = train.data_statistics(msa, Q, cfg)
     h0, J0 = train.profile_init(stats)
     m = bm.bm_potts_load(h0, J0)
-    bm.bm_model_set_engine(m, {"simt": bm.BM_ENGINE_SIMT, "mma": bm.BM_ENGINE_MMA}[engine])
+    bm.bm_model_set_engine(m, {"simt": bm.BM_ENGINE_SIMT, "mma": bm.BM_ENGINE_MMA,
+                               "mma_pair": bm.BM_ENGINE_MMA_PAIR}[engine])
     c = bm.bm_chains_init(m, M, 3)
     hist = train.train(m, c, stats, cfg)
     bm.bm_device_status(m)
