@@ -655,19 +655,43 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     }
                 }
                 for (int k = 0; k < sg.n; ++k) {
+                    const int c = seg_chunk(sg, k);
+                    const int k0 = c * kKC;
+                    // Main chunks touching at most 8 sites (q >= 8): the positions of
+                    // the row's nonzeros are found before the slot wait, with
+                    // independent loads, so only the stores remain after it.
+                    const int jlo = jtab[2 * c], jhi = jtab[2 * c + 1];
+                    const bool fast = !sg.delta && jhi - jlo < 8;
+                    int fpos[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int jj = jlo + t;
+                        fpos[t] = -1;
+                        if (fast && own && jj <= jhi) {
+                            const uint8_t *src = strow + jj;
+                            src = (jj >= s0lo && jj < s0hi) ? ps0 + (jj - s0lo) : src;
+                            src = (jj >= s1lo && jj < s1hi) ? ps1 + (jj - s1lo) : src;
+                            fpos[t] = jj * q + *src - k0;
+                        }
+                    }
                     if (lap > 0 && !mbar_wait(empty_b + 8 * sb, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
                         ok = false;
                         break;
                     }
-                    const int c = seg_chunk(sg, k);
-                    const int k0 = c * kKC;
                     unsigned char *rowp = row0 + sb * NC * 128;
                     if (own) {
 #pragma unroll
                         for (int pc = 0; pc < 8; ++pc)
                             *reinterpret_cast<uint4 *>(rowp + pc * 128) = make_uint4(0, 0, 0, 0);
-                        if (!sg.delta) {
-                            const int jlo = jtab[2 * c], jhi = jtab[2 * c + 1];
+                        if (fast) {
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                const int pos = fpos[t];
+                                if (pos >= 0 && pos < kKC)
+                                    *reinterpret_cast<unsigned short *>(rowp + (pos >> 3) * 128 + (pos & 7) * 2) =
+                                        0x3c00u;
+                            }
+                        } else if (!sg.delta) {
                             for (int jj = jlo; jj <= jhi; ++jj) {
                                 const int sj = (jj >= s0lo && jj < s0hi)   ? ps0[jj - s0lo]
                                                : (jj >= s1lo && jj < s1hi) ? ps1[jj - s1lo]
