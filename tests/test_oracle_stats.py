@@ -267,3 +267,37 @@ def test_update_is_log_likelihood_gradient(orc, point):
                     assert abs((J2[j, i, b, a] - J[j, i, b, a]) / lr - g) < 1e-7
     # the step is not vacuous: the data differ from the model
     assert np.abs(h2 - h).max() > 1e-3 and np.abs(J2 - J).max() > 1e-3
+
+
+def test_update_iterates_to_generating_model(orc):
+    """Iterating Eq. 5 on exact statistics recovers the model that generated
+    them: the data side is the exact enumeration of a planted model (L=3,
+    q=3, no pseudocount), the model side at every step the exact enumeration
+    of the current parameters (as integer counts scaled by K = 2^24, exact to
+    6e-8). From h = J = 0 the iteration must reach the planted model up to
+    gauge: equal energy differences E(s) - E(s0) over all 27 states."""
+    L, q, K = 3, 3, 1 << 24
+    S_all = all_states(L, q)
+    h0, J0 = synth.planted_local_model(L, q, 21, sigma_h=0.8, sigma_J=0.8)
+    h0, J0 = h0.astype(np.float64), J0.astype(np.float64)
+
+    def probs(h, J):
+        e = -orc.energy(h, J, S_all)
+        w = np.exp(e - e.max())
+        return w / w.sum()
+
+    fi, fij = orc.data_stats(S_all, probs(h0, J0), q, 0.0)
+    X = np.zeros((S_all.shape[0], L, q))
+    X[np.arange(S_all.shape[0])[:, None], np.arange(L)[None, :], S_all] = 1.0
+    h, J = np.zeros((L, q)), np.zeros((L, L, q, q))
+    for _ in range(3000):
+        pij = np.einsum("s,sia,sjb->ijab", probs(h, J), X, X)
+        C = np.zeros((orc.n_blocks(L), q, q), dtype=np.int64)
+        for i in range(L):
+            for j in range(i, L):
+                C[orc.block_index(L, i, j)] = np.rint(K * pij[i, j])
+        h, J = orc.update(h, J, fi, fij, C.astype(np.int32), K, 1.0)
+    dE = orc.energy(h, J, S_all) - orc.energy(h, J, S_all[:1])
+    dE0 = orc.energy(h0, J0, S_all) - orc.energy(h0, J0, S_all[:1])
+    assert np.abs(dE - dE0).max() < 1e-3, np.abs(dE - dE0).max()
+    assert np.abs(dE0).max() > 1.0  # the planted model is far from uniform
