@@ -325,13 +325,19 @@ int bm_fields(bm_model m, const uint8_t *seqs_dev, int n, float *H_dev, int form
 /*
  * Batched sweeps of many independent models (uneven-L training of many
  * models on one GPU).  A batch groups (model, chains) pairs with the same q;
- * bm_batch_sweep runs nsweeps CUDA-core sweeps of every pair in ONE launch
- * over a work list of chain tiles (longest models first), replayed from a
- * captured CUDA graph that first refreshes the list (current parameter
- * pointers, sweep counters) from host memory.  The states drawn equal those
- * of bm_gibbs_sweep with BM_ENGINE_SIMT on each pair separately (same
- * Philox uniforms, same FP32 summation order).  The handles stay owned by
- * the caller and must outlive the batch; chains sweep counters advance.
+ * bm_batch_sweep runs nsweeps sweeps of every pair in ONE launch over a work
+ * list of chain tiles, longest models first.  Two forms:
+ *  - tensor cores, when every model's engine resolves to a tensor-core form
+ *    (bm_model_sweep_engine) and every model fits: the two-CTA sweep, one
+ *    cluster per (model, tile), each cluster reading its model's arguments
+ *    and TMA descriptor from the list (refreshed from host memory by each
+ *    call); the arithmetic per chain is that of BM_ENGINE_MMA_PAIR;
+ *  - otherwise CUDA cores, replayed from a captured CUDA graph that first
+ *    refreshes the list (current parameter pointers, sweep counters); the
+ *    states drawn equal those of bm_gibbs_sweep with BM_ENGINE_SIMT on each
+ *    pair separately (same Philox uniforms, same FP32 summation order).
+ * The handles stay owned by the caller and must outlive the batch; chains
+ * sweep counters advance.
  */
 typedef struct bm_batch_s *bm_batch;
 
@@ -340,16 +346,19 @@ typedef struct bm_batch_s *bm_batch;
 int bm_batch_create(const bm_model *models, const bm_chains *chains, int count, bm_batch *out);
 int bm_batch_free(bm_batch b);
 
-/* Times every fitting tile shape (chains per CTA x pipeline stages) on
- * scratch copies of the states (the chains do not move) and keeps the
- * fastest.  Synchronises `stream`. */
+/* Times every fitting tile shape (CUDA cores: chains per CTA x pipeline
+ * stages; tensor cores: the cap on chains per cluster) on scratch copies of
+ * the states (the chains do not move) and keeps the fastest.  Synchronises
+ * `stream`. */
 int bm_batch_autotune(bm_batch b, void *stream);
 
 /* nsweeps sweeps at inverse temperature beta of every pair (one graph
  * launch on `stream`). */
 int bm_batch_sweep(bm_batch b, int nsweeps, float beta, void *stream);
 
-/* Current tile shape: chains per CTA, pipeline stages, CTAs per launch. */
+/* Current tile shape: chains per CTA (per cluster in the tensor-core form),
+ * pipeline stages (one-hot ring slots in the tensor-core form), CTAs per
+ * launch. */
 int bm_batch_shape(bm_batch b, int *chains_per_cta, int *stages, int *ctas);
 
 /*

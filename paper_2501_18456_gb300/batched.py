@@ -4,9 +4,11 @@ together (bm_batch_*), against one launch per model.
 Workload (the batched configuration): 64 models, L ~ U[50, 512], q = 21,
 M = 2048 chains each, planted local models (h ~ N(0, 0.5^2), J ~ N(0,
 0.05^2) for 1 <= |i-j| <= 3), 10 sweeps per iteration.  Reported: aggregate
-site-updates/s of (a) the batched graph launch (autotuned tile shape),
-(b) 64 sequential launches of the plain FP32 CUDA-core sweep, (c) 64
-sequential launches with the default engine (tensor cores where q >= 10).
+site-updates/s of (a) the batched launch in the default (tensor-core) form,
+autotuned, (b) the batched launch in the CUDA-core form (graph replay,
+autotuned), (c) 64 sequential launches of the plain FP32 CUDA-core sweep,
+(d) 64 sequential launches with the default engine (tensor cores where
+q >= 10).
 
 This module only builds inputs and times the library's entry points.
 """
@@ -52,6 +54,14 @@ def run(count: int = 64, M: int = 2048, nsweeps: int = 10, seed: int = 0) -> dic
     batch.autotune()
     t_batch = _time(lambda: batch.sweep(nsweeps, 1.0))
     shape = batch.shape()
+    batch.close()
+    for m in models:
+        bmdca.bm_model_set_engine(m, bmdca.BM_ENGINE_SIMT)
+    batch_cc = bmdca.Batch(models, chains)
+    batch_cc.autotune()
+    t_batch_cc = _time(lambda: batch_cc.sweep(nsweeps, 1.0))
+    shape_cc = batch_cc.shape()
+    batch_cc.close()
 
     def per_model(engine):
         for m in models:
@@ -66,11 +76,12 @@ def run(count: int = 64, M: int = 2048, nsweeps: int = 10, seed: int = 0) -> dic
     t_auto = _time(per_model(bmdca.BM_ENGINE_AUTO))
     for m in models:
         bmdca.bm_device_status(m)
-    batch.close()
     return {"models": count, "chains_per_model": M, "nsweeps": nsweeps,
             "L_min": min(c.L for c in chains), "L_max": max(c.L for c in chains),
             "site_updates_per_iter": units,
-            "batched": {"ms": t_batch, "site_updates_per_s": units / (t_batch * 1e-3), **shape},
+            "batched": {"ms": t_batch, "site_updates_per_s": units / (t_batch * 1e-3), "form": "tensor cores",
+                        **shape},
+            "batched_cuda_cores": {"ms": t_batch_cc, "site_updates_per_s": units / (t_batch_cc * 1e-3), **shape_cc},
             "sequential_plain_fp32": {"ms": t_plain, "site_updates_per_s": units / (t_plain * 1e-3)},
             "sequential_default_engine": {"ms": t_auto, "site_updates_per_s": units / (t_auto * 1e-3)},
             "speedup_vs_plain": t_plain / t_batch}

@@ -140,6 +140,14 @@ int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M);
 int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
 int bm_gibbs_pair_chains_per_cluster(const bm_model_s *m, int M);
 int bm_gibbs_pair_waves(const bm_model_s *m, int M);
+// Batches of (model, chains) pairs swept by the two-CTA tensor-core kernel
+// in one launch over a work list of chain tiles.
+struct bm_pair_batch_s;
+int bm_pair_batch_create(bm_model_s *const *models, bm_chains_s *const *chains, int count, bm_pair_batch_s **out);
+void bm_pair_batch_free(bm_pair_batch_s *b);
+int bm_pair_batch_sweep(bm_pair_batch_s *b, int nsweeps, float beta, cudaStream_t st, uint8_t *const *states_override);
+int bm_pair_batch_autotune(bm_pair_batch_s *b, cudaStream_t st);
+void bm_pair_batch_shape(const bm_pair_batch_s *b, int *nc, int *ctas);
 int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
 // Tensor-core sweep form for this model and chain count: 2 = two-CTA
 // clusters, 1 = one CTA, 0 = CUDA cores (the model's engine, AUTO resolved).

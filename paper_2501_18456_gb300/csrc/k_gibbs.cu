@@ -525,6 +525,7 @@ struct bm_batch_s {
     int next = 0;
     std::vector<int> order;                          // model index of each tile, LPT order
     std::vector<long long> first;                    // first chain of each tile
+    bm_pair_batch_s *pair = nullptr;                 // tensor-core form (then nothing above is used)
 };
 
 namespace {
@@ -670,6 +671,13 @@ int bm_batch_create(const bm_model *models, const bm_chains *chains, int count, 
         b->Lmax = std::max(b->Lmax, m->L);
         b->nsm = m->num_sms > 0 ? m->num_sms : 1;
     }
+    // tensor-core form when every model's engine resolves to the tensor cores
+    bool tc = true;
+    for (int k = 0; k < count; ++k) tc = tc && bm_sweep_form(b->models[k], b->chains[k]->M) != 0;
+    if (tc && bm_pair_batch_create(b->models.data(), b->chains.data(), count, &b->pair) == BM_OK) {
+        *out = b;
+        return BM_OK;
+    }
     // default shape: the largest chains-per-CTA that fits with 3 stages
     int rc = bm_fail(BM_EINVAL, "bm_batch_create: L=%d does not fit shared memory", b->Lmax);
     for (int cpc : {124, 96, 64, 48, 32, 16, 8}) {
@@ -698,6 +706,7 @@ int bm_batch_create(const bm_model *models, const bm_chains *chains, int count, 
 int bm_batch_free(bm_batch b)
 {
     if (!b) return BM_OK;
+    bm_pair_batch_free(b->pair);
     drop_graphs(b);
     for (auto &e : b->used)
         if (e) cudaEventDestroy(e);
@@ -711,7 +720,8 @@ int bm_batch_sweep(bm_batch b, int nsweeps, float beta, void *stream)
     if (nsweeps < 0) return bm_fail(BM_EINVAL, "bm_batch_sweep: nsweeps=%d < 0", nsweeps);
     if (!isfinite(beta)) return bm_fail(BM_EINVAL, "bm_batch_sweep: beta not finite");
     if (nsweeps == 0) return BM_OK;
-    const int rc = launch_graph(b, nsweeps, beta, (cudaStream_t)stream, nullptr);
+    const int rc = b->pair ? bm_pair_batch_sweep(b->pair, nsweeps, beta, (cudaStream_t)stream, nullptr)
+                           : launch_graph(b, nsweeps, beta, (cudaStream_t)stream, nullptr);
     if (rc != BM_OK) return rc;
     for (auto *c : b->chains) c->sweep += (uint64_t)nsweeps;
     return BM_OK;
@@ -721,6 +731,11 @@ int bm_batch_autotune(bm_batch b, void *stream)
 {
     if (!b) return bm_fail(BM_EINVAL, "bm_batch_autotune: NULL batch");
     cudaStream_t st = (cudaStream_t)stream;
+    if (b->pair) {
+        const int rc = bm_pair_batch_autotune(b->pair, st);
+        b->tuned = rc == BM_OK;
+        return rc;
+    }
     // scratch copies of the states: tuning sweeps must not move the chains
     std::vector<uint8_t *> scratch(b->chains.size(), nullptr);
     int rc = BM_OK;
@@ -770,6 +785,11 @@ int bm_batch_autotune(bm_batch b, void *stream)
 int bm_batch_shape(bm_batch b, int *chains_per_cta, int *stages, int *ctas)
 {
     if (!b) return bm_fail(BM_EINVAL, "bm_batch_shape: NULL batch");
+    if (b->pair) {
+        bm_pair_batch_shape(b->pair, chains_per_cta, ctas);
+        if (stages) *stages = 2;  // one-hot operand ring of the tensor-core form
+        return BM_OK;
+    }
     if (chains_per_cta) *chains_per_cta = b->shape.cpc;
     if (stages) *stages = b->shape.ns;
     if (ctas) *ctas = b->nitems;

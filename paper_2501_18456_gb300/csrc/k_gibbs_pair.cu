@@ -18,10 +18,12 @@
 // its MMAs are twice as wide (N = NC), so the shared-memory bandwidth that
 // bounds the single-CTA form buys about twice the MMA work per byte.
 //
-// Exchange.  Each new state a drawer picks is also stored into the peer's
-// copy (st.shared::cluster).  After a block every drawer thread arrives on
-// the peer's ready barrier of that block's parity with release semantics at
-// cluster scope; waiters acquire at cluster scope.  Schedule of pair P in
+// Exchange.  After redrawing a block each drawer thread copies its chain's
+// new states of the block into the peer's copy (st.shared::cluster) and
+// arrives on the peer's ready barrier of that block's parity with release
+// semantics at cluster scope; waiters acquire at cluster scope.  CTA 0 makes
+// that copy of block 2P only once CTA 1's generators have finished pair P's
+// main chunks (gen_done), which read block 2P's pre-redraw states.  Schedule of pair P in
 // CTA r, each step a run of 64-column K chunks:
 //   A  main chunks [0, X) into block 2P+r: states after block 2P-3, with
 //      blocks 2P-2 and 2P-1 (being redrawn) from their pre-redraw snapshots;
@@ -57,7 +59,10 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <new>
+#include <vector>
 
 using namespace bmtc;
 
@@ -76,7 +81,7 @@ constexpr int kDraw = 32 * kDrawWarps;  // drawer threads
 constexpr int kGen = 32 * kGenWarps;    // generator threads
 constexpr int kThreads = 64 + kDraw + kGen;
 constexpr int kNCmax = 160;
-constexpr int kNBars = 2 * kNA + 2 * kNB + 2 + 2 + 2 + 1 + 1;
+constexpr int kNBars = 2 * kNA + 2 * kNB + 2 + 2 + 2 + 1 + 1 + 1;
 
 // ---------------------------------------------------------------- cluster helpers
 __device__ __forceinline__ uint32_t cluster_rank()
@@ -184,6 +189,15 @@ struct PairArgs {
     int M, L, q, Lp, B, nb, nK, X, NC;
     long long nblocks;
     uint32_t tmem_cols, acc_stride;
+};
+
+// One cluster's work in a batch of models: the model's arguments, its
+// coupling tensor map (a TMA descriptor in device memory; the struct takes
+// CUtensorMap's alignment) and the first chain of the cluster's tile.
+struct PairItem {
+    CUtensorMap tm;
+    PairArgs a;
+    long long first;
 };
 
 __host__ __device__ inline int st_stride(int Lp) { return Lp + 4; }
@@ -301,9 +315,16 @@ __device__ Seg seg_info(const PairArgs &p, long long P, int step, int r)
     return s;
 }
 
+// BATCH: cluster k runs items[k] (its own model, tensor map and chain tile);
+// otherwise every cluster runs the launch arguments on chains k*NC ...
+template <bool BATCH>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
-    k_gibbs_pair(const __grid_constant__ CUtensorMap tm_jp, const PairArgs p)
+    k_gibbs_pair(const __grid_constant__ CUtensorMap tm_one, const __grid_constant__ PairArgs p_one,
+                 const PairItem *__restrict__ items)
 {
+    const PairItem *const item = BATCH ? items + (blockIdx.x >> 1) : nullptr;
+    const PairArgs &p = BATCH ? item->a : p_one;
+    const CUtensorMap *const tm_jp = BATCH ? &item->tm : &tm_one;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = su32(smem_raw);
     unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -324,11 +345,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const uint32_t ready = acc_empty + 16;        // [2], states after block kb: barrier kb % 2
     const uint32_t snapready = ready + 16;        // CTA 0: next pair's snapshots taken
     const uint32_t corr_bar = snapready + 8;      // staged coupling blocks of the own block
+    const uint32_t gen_done = corr_bar + 8;       // CTA 0: CTA 1's generators finished pair P's main chunks
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = (int)cluster_rank(), peer = r ^ 1;
     const int q = p.q, L = p.L, NC = p.NC, Lp = p.Lp;
     const int Sst = st_stride(Lp), Ssn = snap_stride(p.B);
-    const size_t cta0 = (size_t)(blockIdx.x >> 1) * NC;
+    const size_t cta0 = BATCH ? (size_t)item->first : (size_t)(blockIdx.x >> 1) * NC;
     const long long nblocks = p.nblocks;
     const long long npairs = (nblocks + 1) / 2;
     auto snap_of = [&](long long kb) { return snap + (size_t)((((kb >> 1) & 1) * 2 + (kb & 1)) * NC) * Ssn; };
@@ -349,6 +371,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
         mbar_init(snapready, kDraw);
         mbar_init(corr_bar, 1);
+        mbar_init(gen_done, kGenWarps);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -412,7 +435,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         }
                         const uint32_t dst = su32(base + lay.a + sa * kSlotA), bar = full_a + 8 * sa;
                         mbar_expect_tx(bar, (uint32_t)kSlotA);
-                        tma_load_3d(dst, &tm_jp, 0, r0, 2 * c, bar);  // hi slab then lo slab of 128 rows
+                        tma_load_3d(dst, tm_jp, 0, r0, 2 * c, bar);  // hi slab then lo slab of 128 rows
                         ++issued;
                         if (++sa == kNA) {
                             sa = 0;
@@ -577,7 +600,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     for (int a = 31; a >= 0; --a)
                         if (a < q && thr < H[a]) pick = a;
                     st[ch * Sst + i] = (uint8_t)pick;
-                    st_cluster_u8(st_peer + (uint32_t)(ch * Sst + i), (unsigned short)pick);
                 }
                 named_bar_sync(1, kDraw);  // Hs is rewritten for the next site
             }
@@ -602,6 +624,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         for (int x = 0; x < gn.Bk; ++x) sn[x] = st[w * Sst + gn.i0 + x];
                     }
             }
+            // Copy block kb's new states into the peer's copy.  CTA 0 first waits
+            // until CTA 1's generators have finished pair j's main chunks, which
+            // still read block kb's pre-redraw states from CTA 1's copy.
+            if (r == 0 && ok && !mbar_wait_cl(gen_done, (uint32_t)(j & 1), abort_flag, p.err)) ok = false;
+            if (ok && w < NC)
+                for (int x = 0; x < g.Bk; ++x)
+                    st_cluster_u8(st_peer + (uint32_t)(w * Sst + g.i0 + x), (unsigned short)st[w * Sst + g.i0 + x]);
             // publish block kb: own generator and the peer
             mbar_arrive(ready + 8 * (int)(kb & 1));
             mbar_arrive_peer(ready_peer + 8 * (uint32_t)(kb & 1));
@@ -631,6 +660,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         unsigned char *const row0 = base + lay.b + noswz_off(own ? w : 0, 0);
         const uint8_t *const strow = st + (own ? w : 0) * Sst;
         const int wrow = (own ? w : 0) * Ssn;
+        const uint32_t gen_done_peer = peer_addr(gen_done, (uint32_t)peer);
         int sb = 0, lap = 0;
         bool ok = true;
         for (long long P = 0; P <= npairs && ok; ++P) {
@@ -730,6 +760,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         ++lap;
                     }
                 }
+                // CTA 1: pair P's main chunks are read; CTA 0 may now overwrite
+                // block 2P's sites in this CTA's copy of the states
+                if (ok && r == 1 && step == 2 && 2 * P < nblocks) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_peer(gen_done_peer);
+                }
             }
         }
         if (!ok) *abort_flag = 1;
@@ -801,13 +837,14 @@ int max_clusters(const bm_model_s *m)
     std::call_once(g_clusters_once[dev], [&] {
         int n = (m->num_sms > 0 ? m->num_sms : 2) / 2;
         const int smem = 200 * 1024;  // any size above half an SM's shared memory: one CTA per SM
-        if (cudaFuncSetAttribute(k_gibbs_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess) {
+        if (cudaFuncSetAttribute(k_gibbs_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+            cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(2, 1, 1);
             cfg.blockDim = dim3(kThreads, 1, 1);
             cfg.dynamicSmemBytes = smem;
             int c = 0;  // the kernel's cluster shape (2 CTAs) is fixed at compile time
-            if (cudaOccupancyMaxActiveClusters(&c, k_gibbs_pair, &cfg) == cudaSuccess && c > 0) n = c;
+            if (cudaOccupancyMaxActiveClusters(&c, k_gibbs_pair<false>, &cfg) == cudaSuccess && c > 0) n = c;
         }
         (void)cudaGetLastError();
         g_max_clusters[dev] = n > 0 ? n : 1;
@@ -815,47 +852,32 @@ int max_clusters(const bm_model_s *m)
     return g_max_clusters[dev];
 }
 
-}  // namespace
-
-// Chains per cluster for the two-CTA tensor-core sweep (multiple of 16,
-// <= 160), or 0 when the shape does not fit one CTA's shared memory or L < 2.
-int bm_gibbs_pair_chains_per_cluster(const bm_model_s *m, int M)
+// Largest chains per cluster (multiple of 16, <= min(cap, 160)) whose layout
+// fits one CTA's shared memory; 0 when none does or the shape is unsupported.
+int fit_nc(const bm_model_s *m, int cap)
 {
     if (m->L < 2 || m->L > 65535 || m->q > kQmax) return 0;
     const int B = bm_split_block_sites(m->L, m->q);
     if (B > kBmax) return 0;
-    const int ncl = max_clusters(m);
-    int nc = (M + ncl - 1) / ncl;
-    nc = std::max(16, (nc + 15) & ~15);
-    nc = std::min(nc, kNCmax);
     const int Lp = (m->L + 15) & ~15;
     const int nK = (m->L * m->q + kKC - 1) / kKC;
+    int nc = std::min(cap, kNCmax) & ~15;
     while (nc >= 16 && smem_layout(nc, Lp, B, nK, m->q).total + 1024 > 227 * 1024) nc -= 16;
     return nc >= 16 ? nc : 0;
 }
 
-// Waves of clusters the two-CTA sweep of M chains needs (0: does not fit).
-int bm_gibbs_pair_waves(const bm_model_s *m, int M)
+size_t smem_bytes(const bm_model_s *m, int nc)
 {
-    const int nc = bm_gibbs_pair_chains_per_cluster(m, M);
-    if (nc == 0) return 0;
-    const int ncl = max_clusters(m);
-    return ((M + nc - 1) / nc + ncl - 1) / ncl;
+    const int B = bm_split_block_sites(m->L, m->q);
+    return (size_t)smem_layout(nc, (m->L + 15) & ~15, B, (m->L * m->q + kKC - 1) / kKC, m->q).total + 1024;
 }
 
-int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)
+void fill_args(const bm_model_s *m, const bm_chains_s *c, int NC, int nsweeps, float beta, uint8_t *states,
+               PairArgs &a)
 {
-    const int NC = bm_gibbs_pair_chains_per_cluster(m, c->M);
-    if (NC == 0) return bm_fail(BM_EINVAL, "two-CTA tensor-core sweep: shape does not fit shared memory");
-    {
-        int rc = bm_split_prepare(m, 0, st);
-        if (rc == BM_OK) rc = corr_prepare(m, bm_split_block_sites(c->L, c->q), st);
-        if (rc != BM_OK) return rc;
-    }
-    PairArgs a;
     a.h = m->h;
     a.Jc = m->Jc;
-    a.states = c->s;
+    a.states = states;
     a.err = m->dflags + 3;
     a.seed = c->seed;
     a.sweep0 = c->sweep;
@@ -873,11 +895,216 @@ int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta,
     a.X = a.nK / 2;
     a.acc_stride = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;
     a.tmem_cols = 2 * a.acc_stride;
-    const Smem lay = smem_layout(NC, a.Lp, a.B, a.nK, a.q);
-    const size_t smem = lay.total + 1024;
-    BM_CK(cudaFuncSetAttribute(k_gibbs_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+}
+
+// The tensor-core layouts (split J, in-block corrections) of the live J.
+int model_prepare(bm_model_s *m, cudaStream_t st)
+{
+    int rc = bm_split_prepare(m, 0, st);
+    if (rc == BM_OK) rc = corr_prepare(m, bm_split_block_sites(m->L, m->q), st);
+    return rc;
+}
+
+}  // namespace
+
+// Chains per cluster for the two-CTA tensor-core sweep (multiple of 16,
+// <= 160), or 0 when the shape does not fit one CTA's shared memory or L < 2.
+int bm_gibbs_pair_chains_per_cluster(const bm_model_s *m, int M)
+{
+    const int ncl = max_clusters(m);
+    const int want = std::max(16, (((M + ncl - 1) / ncl) + 15) & ~15);
+    return fit_nc(m, want);
+}
+
+// Waves of clusters the two-CTA sweep of M chains needs (0: does not fit).
+int bm_gibbs_pair_waves(const bm_model_s *m, int M)
+{
+    const int nc = bm_gibbs_pair_chains_per_cluster(m, M);
+    if (nc == 0) return 0;
+    const int ncl = max_clusters(m);
+    return ((M + nc - 1) / nc + ncl - 1) / ncl;
+}
+
+int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)
+{
+    const int NC = bm_gibbs_pair_chains_per_cluster(m, c->M);
+    if (NC == 0) return bm_fail(BM_EINVAL, "two-CTA tensor-core sweep: shape does not fit shared memory");
+    {
+        const int rc = model_prepare(m, st);
+        if (rc != BM_OK) return rc;
+    }
+    PairArgs a;
+    fill_args(m, c, NC, nsweeps, beta, c->s, a);
+    const size_t smem = smem_bytes(m, NC);
+    BM_CK(cudaFuncSetAttribute(k_gibbs_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nclusters = (c->M + NC - 1) / NC;
-    k_gibbs_pair<<<2 * nclusters, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(m->tmap_jp), a);
+    k_gibbs_pair<false><<<2 * nclusters, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(m->tmap_jp), a,
+                                                                nullptr);
     BM_CK_LAUNCH("k_gibbs_pair");
     return BM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of models: one launch, cluster k runs work item k = (model, chain
+// tile), items ordered longest model first (LPT).  A model's tile size is the
+// largest chain count its layout fits (fewer clusters stream its couplings),
+// capped by an autotuned limit, and balanced over its tiles.
+// ---------------------------------------------------------------------------
+struct bm_pair_batch_s {
+    std::vector<bm_model_s *> models;
+    std::vector<bm_chains_s *> chains;
+    int cap = kNCmax;
+    std::vector<int> model_of, nc_of;
+    std::vector<long long> first;
+    size_t smem = 0;
+    int ncmax = 0;
+    PairItem *items_dev = nullptr, *items_host = nullptr;
+    size_t items_cap = 0;
+    cudaEvent_t used = nullptr;  // the copy of items_host made by the last launch
+};
+
+namespace {
+
+int build_tiles(bm_pair_batch_s *b)
+{
+    std::vector<int> idx(b->models.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = (int)k;
+    std::stable_sort(idx.begin(), idx.end(), [b](int x, int y) { return b->models[x]->L > b->models[y]->L; });
+    b->model_of.clear();
+    b->nc_of.clear();
+    b->first.clear();
+    b->smem = 0;
+    b->ncmax = 0;
+    for (int k : idx) {
+        const bm_model_s *m = b->models[k];
+        const int M = b->chains[k]->M;
+        const int fit = fit_nc(m, b->cap);
+        if (fit == 0) return bm_fail(BM_EINVAL, "batch: L=%d q=%d does not fit the tensor-core sweep", m->L, m->q);
+        const int tiles = (M + fit - 1) / fit;
+        const int nc = std::min(fit, (((M + tiles - 1) / tiles) + 15) & ~15);
+        for (long long c0 = 0; c0 < M; c0 += nc) {
+            b->model_of.push_back(k);
+            b->nc_of.push_back(nc);
+            b->first.push_back(c0);
+        }
+        b->smem = std::max(b->smem, smem_bytes(m, nc));
+        b->ncmax = std::max(b->ncmax, nc);
+    }
+    const size_t n = b->model_of.size();
+    if (n > b->items_cap) {
+        if (b->used) cudaEventSynchronize(b->used);
+        cudaFree(b->items_dev);
+        cudaFreeHost(b->items_host);
+        b->items_dev = nullptr;
+        b->items_host = nullptr;
+        b->items_cap = 0;
+        BM_CK(cudaMalloc(&b->items_dev, n * sizeof(PairItem)));
+        BM_CK(cudaMallocHost(&b->items_host, n * sizeof(PairItem)));
+        b->items_cap = n;
+    }
+    return BM_OK;
+}
+
+}  // namespace
+
+int bm_pair_batch_create(bm_model_s *const *models, bm_chains_s *const *chains, int count, bm_pair_batch_s **out)
+{
+    *out = nullptr;
+    bm_pair_batch_s *b = new (std::nothrow) bm_pair_batch_s();
+    if (!b) return bm_fail(BM_ENOMEM, "batch: host allocation failed");
+    b->models.assign(models, models + count);
+    b->chains.assign(chains, chains + count);
+    int rc = build_tiles(b);
+    if (rc == BM_OK && cudaEventCreateWithFlags(&b->used, cudaEventDisableTiming) != cudaSuccess)
+        rc = bm_fail(BM_ECUDA, "batch: event");
+    if (rc != BM_OK) {
+        bm_pair_batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return BM_OK;
+}
+
+void bm_pair_batch_free(bm_pair_batch_s *b)
+{
+    if (!b) return;
+    if (b->used) {
+        cudaEventSynchronize(b->used);
+        cudaEventDestroy(b->used);
+    }
+    cudaFree(b->items_dev);
+    cudaFreeHost(b->items_host);
+    delete b;
+}
+
+int bm_pair_batch_sweep(bm_pair_batch_s *b, int nsweeps, float beta, cudaStream_t st, uint8_t *const *states_override)
+{
+    for (auto *m : b->models) {
+        const int rc = model_prepare(m, st);
+        if (rc != BM_OK) return rc;
+    }
+    const int n = (int)b->model_of.size();
+    BM_CK(cudaEventSynchronize(b->used));  // the previous launch's copy of the list has been made
+    for (int t = 0; t < n; ++t) {
+        const int k = b->model_of[t];
+        PairItem &it = b->items_host[t];
+        std::memcpy(&it.tm, b->models[k]->tmap_jp, sizeof(CUtensorMap));
+        fill_args(b->models[k], b->chains[k], b->nc_of[t], nsweeps, beta,
+                  states_override ? states_override[k] : b->chains[k]->s, it.a);
+        it.first = b->first[t];
+    }
+    BM_CK(cudaMemcpyAsync(b->items_dev, b->items_host, (size_t)n * sizeof(PairItem), cudaMemcpyHostToDevice, st));
+    BM_CK(cudaEventRecord(b->used, st));
+    BM_CK(cudaFuncSetAttribute(k_gibbs_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    k_gibbs_pair<true><<<2 * n, kThreads, b->smem, st>>>(b->items_host[0].tm, b->items_host[0].a, b->items_dev);
+    BM_CK_LAUNCH("k_gibbs_pair (batch)");
+    return BM_OK;
+}
+
+int bm_pair_batch_autotune(bm_pair_batch_s *b, cudaStream_t st)
+{
+    // tuning sweeps run on scratch copies of the states: the chains do not move
+    std::vector<uint8_t *> scratch(b->chains.size(), nullptr);
+    int rc = BM_OK;
+    for (size_t k = 0; k < b->chains.size() && rc == BM_OK; ++k) {
+        const size_t n = (size_t)b->chains[k]->M * b->chains[k]->L;
+        cudaError_t e = cudaMalloc(&scratch[k], n);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(scratch[k], b->chains[k]->s, n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) rc = bm_cuda_fail(e, "batch autotune: scratch");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == BM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = bm_fail(BM_ECUDA, "batch autotune: events");
+    int best = b->cap;
+    float best_ms = 1e30f;
+    for (int cap : {160, 128, 96, 64, 48, 32}) {
+        if (rc != BM_OK) break;
+        b->cap = cap;
+        rc = build_tiles(b);
+        if (rc == BM_OK) rc = bm_pair_batch_sweep(b, 1, 1.0f, st, scratch.data());  // warm-up
+        if (rc == BM_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = bm_fail(BM_ECUDA, "batch autotune: event");
+        for (int r = 0; r < 2 && rc == BM_OK; ++r) rc = bm_pair_batch_sweep(b, 1, 1.0f, st, scratch.data());
+        if (rc == BM_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = bm_fail(BM_ECUDA, "batch autotune: event");
+        float ms = 0.0f;
+        if (rc == BM_OK &&
+            (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = bm_fail(BM_ECUDA, "batch autotune: timing");
+        if (rc == BM_OK && ms < best_ms) {
+            best_ms = ms;
+            best = cap;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    for (auto *p : scratch) cudaFree(p);
+    b->cap = best;
+    const int rc2 = build_tiles(b);
+    return rc == BM_OK ? rc2 : rc;
+}
+
+void bm_pair_batch_shape(const bm_pair_batch_s *b, int *nc, int *ctas)
+{
+    if (nc) *nc = b->ncmax;
+    if (ctas) *ctas = 2 * (int)b->model_of.size();
 }

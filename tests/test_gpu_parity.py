@@ -174,6 +174,30 @@ def test_gibbs_config2_launch_sampled_chains(bm, orc, engine):
         assert bad == 0 or worst < FLIP_MARGIN, (k, bad, worst)
 
 
+@pytest.mark.parametrize("L,M", [(512, 300), (400, 200), (700, 64)])
+@pytest.mark.parametrize("engine", GIBBS_ENGINES)
+def test_gibbs_long_sequences_teacher_forced(bm, orc, L, M, engine):
+    """Long sequences: the main chunks after a pair's delta step outlast the
+    redraw of the previous blocks, so any state a CTA reads too late (or a
+    peer overwrites too early) shows up as wrong draws near the end of the
+    sweep; every site of sampled chains over two sweeps is checked."""
+    h, J = synth.planted_local_model(L, 21, 13, sigma_h=1.0, sigma_J=0.3)
+    m = load(bm, h, J, engine)
+    c = bm.bm_chains_init(m, M, 31)
+    s0 = states_of(bm, c)
+    bm.bm_gibbs_sweep(m, c, 1, 1.0)
+    s1 = states_of(bm, c)
+    bm.bm_gibbs_sweep(m, c, 1, 1.0)
+    bm.bm_device_status(m)
+    s2 = states_of(bm, c)
+    h64, J64 = h.astype(np.float64), J.astype(np.float64)
+    sample = sorted(set(np.random.default_rng(2).choice(M, min(M, 40), replace=False).tolist()) | {M - 1})
+    for k in sample:
+        for sw, (a, b) in enumerate([(s0, s1), (s1, s2)]):
+            bad, worst, _ = orc.gibbs_verify(h64, J64, a[k:k + 1], b[k:k + 1], 31, sw, 1.0, k)
+            assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
+
+
 @pytest.mark.parametrize("engine", ["mma", "mma_pair"])
 def test_gibbs_more_chains_than_one_wave(bm, orc, engine):
     """M = 12000 chains: more CTAs (clusters) than the GPU runs at once, so
