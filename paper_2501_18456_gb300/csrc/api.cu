@@ -420,11 +420,13 @@ int bm_seq_weights(const uint8_t *msa_dev, int N, int L, double seqid, float *w_
     cudaStream_t st = (cudaStream_t)stream;
     const int thr = (int)ceil(seqid * L - 1e-9);
     void *scratch = nullptr;
-    const size_t bytes = (size_t)N * sizeof(int) + 16;
+    const size_t cnt_bytes = ((size_t)N * sizeof(int) + 255) & ~(size_t)255;
+    const size_t bytes = 256 + cnt_bytes + bm_seq_weights_planes_bytes(N, L);
     BM_CK(cudaMallocAsync(&scratch, bytes, st));
-    int *cnt = (int *)((char *)scratch + 16);
     double *meff_dev = (double *)scratch;
-    int rc = bm_launch_seq_weights(msa_dev, N, L, thr, w_dev, cnt, meff_dev, st);
+    int *cnt = (int *)((char *)scratch + 256);
+    uint32_t *planes = (uint32_t *)((char *)scratch + 256 + cnt_bytes);
+    int rc = bm_launch_seq_weights_bs(msa_dev, N, L, thr, w_dev, cnt, planes, meff_dev, st);
     double meff = 0.0;
     if (rc == BM_OK && meff_host) {
         cudaError_t e = cudaMemcpyAsync(&meff, meff_dev, sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -165,6 +165,11 @@ int bm_launch_chain_stats_mma(const uint8_t *s, int M, int L, int q, int32_t *co
 int bm_launch_chain_stats_tc(bm_chains_s *c, int32_t *counts, cudaStream_t st);
 int bm_launch_seq_weights(const uint8_t *msa, int N, int L, int thr, float *w, int *cnt,
                           double *meff_dev, cudaStream_t st);
+// Bit-sliced form (bm_seq_weights): planes is scratch of
+// bm_seq_weights_planes_bytes(N, L) bytes.
+size_t bm_seq_weights_planes_bytes(int N, int L);
+int bm_launch_seq_weights_bs(const uint8_t *msa, int N, int L, int thr, float *w, int *cnt, uint32_t *planes,
+                             double *meff_dev, cudaStream_t st);
 int bm_launch_data_stats(const uint8_t *msa, const float *w, int N, int L, int q, double alpha,
                          int frac_bits, double meff, float *fi, float *fij,
                          unsigned long long *acc_fi, cudaStream_t st);

@@ -288,6 +288,141 @@ __global__ void __launch_bounds__(256) k_identity(const uint8_t *__restrict__ X,
     }
 }
 
+// ----------------------------------------------------------------------------
+// Bit-sliced identity counts (the same counts as k_identity).  A pre-pass
+// stores every sequence as 8 bit planes of its symbol bytes, 32 positions
+// per word (word w of a sequence = 8 consecutive uint32, plane p holding
+// bit p of the symbols at positions 32w .. 32w+31; zero beyond L), and ORs
+// all symbols into one flag word.  For a pair, OR over the planes of
+// (a_p XOR b_p) marks the positions whose symbols differ, so a word of 32
+// positions costs one logic op per plane and a popcount: identity = L -
+// mismatches.  Planes above the highest bit any symbol uses are all zero
+// and skipped (5 planes for alphabets up to 32 symbols).
+// ----------------------------------------------------------------------------
+constexpr int kBP = 8;        // bit planes stored (symbol bytes)
+constexpr int kBWChunk = 8;   // words (of 32 positions) per staged chunk
+
+// One warp per (sequence, word): lane k holds position 32w + k.
+__global__ void __launch_bounds__(256) k_bitslice(const uint8_t *__restrict__ X, int N, int L, int Lw,
+                                                  uint32_t *__restrict__ planes, unsigned *__restrict__ used)
+{
+    const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp_id >= (long long)N * Lw) return;  // whole warps leave together
+    const int n = (int)(warp_id / Lw), wd = (int)(warp_id % Lw);
+    const int pos = wd * 32 + lane;
+    const uint32_t b = pos < L ? X[(size_t)n * L + pos] : 0u;
+    uint32_t mine = 0, any = 0;
+#pragma unroll
+    for (int pl = 0; pl < kBP; ++pl) {
+        const uint32_t word = __ballot_sync(0xffffffffu, (b >> pl) & 1u);
+        if (lane == pl) mine = word;
+        any |= word ? (1u << pl) : 0u;
+    }
+    if (lane < kBP) planes[((size_t)n * Lw + wd) * kBP + lane] = mine;
+    if (lane == 0 && any) atomicOr(used, any);
+}
+
+// 4 x 4 pairs of one thread over one word: mismatches from the first NP planes.
+template <int NP>
+__device__ __forceinline__ void pair_words(const uint4 (&a)[4][2], const uint4 (&b)[4][2], int (&mism)[4][4])
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const uint32_t pa[8] = {a[u][0].x, a[u][0].y, a[u][0].z, a[u][0].w,
+                                    a[u][1].x, a[u][1].y, a[u][1].z, a[u][1].w};
+            const uint32_t pb[8] = {b[v][0].x, b[v][0].y, b[v][0].z, b[v][0].w,
+                                    b[v][1].x, b[v][1].y, b[v][1].z, b[v][1].w};
+            uint32_t d = pa[0] ^ pb[0];
+#pragma unroll
+            for (int pl = 1; pl < NP; ++pl) d |= pa[pl] ^ pb[pl];
+            mism[u][v] += __popc(d);
+        }
+}
+
+__global__ void __launch_bounds__(256) k_identity_bs(const uint32_t *__restrict__ planes,
+                                                     const unsigned *__restrict__ used, int N, int L, int Lw,
+                                                     int thr, int ntile, int *__restrict__ cnt)
+{
+    constexpr int kRow4 = 2 * kBWChunk + 1;  // uint4 per staged sequence (odd: conflict-free 128-bit reads)
+    __shared__ uint4 A[kWT][kRow4];
+    __shared__ uint4 B[kWT][kRow4];
+    __shared__ int cntA[kWT], cntB[kWT];
+    int tm, tn;
+    tile_pair_from_index(blockIdx.x, ntile, tm, tn);
+    const int m0 = tm * kWT, n0 = tn * kWT;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 4 x 4 pairs each
+    const bool five = (*used >> 5) == 0u;                    // every symbol < 32
+    int mism[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) mism[u][v] = 0;
+    if (threadIdx.x < kWT) {
+        cntA[threadIdx.x] = 0;
+        cntB[threadIdx.x] = 0;
+    }
+    const uint4 *P4 = reinterpret_cast<const uint4 *>(planes);
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (int w0 = 0; w0 < Lw; w0 += kBWChunk) {
+        const int nw = min(kBWChunk, Lw - w0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < kWT * 2 * kBWChunk; k += blockDim.x) {
+            const int r = k / (2 * kBWChunk), c2 = k % (2 * kBWChunk);
+            const int ma = m0 + r, nb = n0 + r;
+            const bool in = (c2 >> 1) < nw;
+            A[r][c2] = (in && ma < N) ? P4[((size_t)ma * Lw + w0) * 2 + c2] : zero;
+            B[r][c2] = (in && nb < N) ? P4[((size_t)nb * Lw + w0) * 2 + c2] : zero;
+        }
+        __syncthreads();
+        for (int c = 0; c < nw; ++c) {
+            uint4 ra[4][2], rb[4][2];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ra[u][0] = A[ty + 16 * u][2 * c];
+                ra[u][1] = A[ty + 16 * u][2 * c + 1];
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                rb[v][0] = B[tx + 16 * v][2 * c];
+                rb[v][1] = B[tx + 16 * v][2 * c + 1];
+            }
+            if (five)
+                pair_words<5>(ra, rb, mism);
+            else
+                pair_words<8>(ra, rb, mism);
+        }
+    }
+    // Credit qualifying pairs (identity = L - mismatches >= thr).
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int rm = ty + 16 * u, rn = tx + 16 * v;
+            const int m = m0 + rm, n = n0 + rn;
+            if (m >= N || n >= N || L - mism[u][v] < thr) continue;
+            if (tm == tn) {
+                if (rm < rn) {
+                    atomicAdd(&cntA[rm], 1);
+                    atomicAdd(&cntB[rn], 1);
+                } else if (rm == rn) {
+                    atomicAdd(&cntA[rm], 1);  // self-identity, counted once
+                }
+            } else {
+                atomicAdd(&cntA[rm], 1);
+                atomicAdd(&cntB[rn], 1);
+            }
+        }
+    __syncthreads();
+    if (threadIdx.x < kWT) {
+        const int m = m0 + threadIdx.x, n = n0 + threadIdx.x;
+        if (m < N && cntA[threadIdx.x]) atomicAdd(&cnt[m], cntA[threadIdx.x]);
+        if (n < N && cntB[threadIdx.x]) atomicAdd(&cnt[n], cntB[threadIdx.x]);
+    }
+}
+
 // w = 1 / N_m; M_eff = sum w in FP64 (one CTA, fixed order => deterministic).
 __global__ void k_weights_finalize(const int *__restrict__ cnt, int N, float *__restrict__ w,
                                    double *meff)
@@ -382,6 +517,31 @@ int bm_launch_weight_sum(const float *w, int N, double *out3, cudaStream_t st)
 {
     k_weight_sum<<<1, 1024, 0, st>>>(w, N, out3);
     BM_CK_LAUNCH("k_weight_sum");
+    return BM_OK;
+}
+
+size_t bm_seq_weights_planes_bytes(int N, int L)
+{
+    return (size_t)N * kBP * ((L + 31) / 32) * sizeof(uint32_t) + 16;  // + the used-bits word
+}
+
+int bm_launch_seq_weights_bs(const uint8_t *msa, int N, int L, int thr, float *w, int *cnt, uint32_t *planes,
+                             double *meff_dev, cudaStream_t st)
+{
+    const int Lw = (L + 31) / 32;
+    unsigned *used = reinterpret_cast<unsigned *>(planes + (size_t)N * kBP * Lw);
+    BM_CK(cudaMemsetAsync(cnt, 0, (size_t)N * sizeof(int), st));
+    BM_CK(cudaMemsetAsync(used, 0, sizeof(unsigned), st));
+    const long long warps = (long long)N * Lw;
+    k_bitslice<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(msa, N, L, Lw, planes, used);
+    BM_CK_LAUNCH("k_bitslice");
+    const int ntile = (N + kWT - 1) / kWT;
+    const long long npairs = (long long)ntile * (ntile + 1) / 2;
+    if (npairs > 0x7fffffffLL) return bm_fail(BM_EINVAL, "bm_seq_weights: N too large");
+    k_identity_bs<<<(unsigned)npairs, 256, 0, st>>>(planes, used, N, L, Lw, thr, ntile, cnt);
+    BM_CK_LAUNCH("k_identity_bs");
+    k_weights_finalize<<<1, 1024, 0, st>>>(cnt, N, w, meff_dev);
+    BM_CK_LAUNCH("k_weights_finalize");
     return BM_OK;
 }
 

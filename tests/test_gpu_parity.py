@@ -347,6 +347,27 @@ def test_seq_weights_special_cases(bm):
     assert bm.bm_seq_weights(to_dev(far), w) == 21.0
 
 
+@pytest.mark.parametrize("top", [32, 256])
+def test_seq_weights_byte_symbols(bm, orc, top):
+    """Weights compare whole symbol bytes: symbols up to 255 (all eight bit
+    planes of the bit-sliced comparison) and exactly 32 (the sixth plane),
+    with near-identical rows so the threshold is exercised."""
+    N, L = 300, 70
+    rng = np.random.default_rng(top)
+    base = rng.integers(0, top, size=(30, L), dtype=np.uint8)
+    X = base[rng.integers(0, 30, size=N)].copy()
+    flip = rng.random((N, L)) < 0.15
+    X[flip] = rng.integers(0, top, size=int(flip.sum()), dtype=np.uint8)
+    if top == 32:
+        X[5, 3] = 32
+    w = torch.empty(N, dtype=torch.float32, device=DEV)
+    meff = bm.bm_seq_weights(to_dev(X), w, 0.8)
+    w_o, meff_o = orc.seq_weights(X, 0.8)
+    assert np.array_equal(w.cpu().numpy(), w_o.astype(np.float32))
+    assert meff == pytest.approx(meff_o, rel=1e-12)
+    assert 1.0 < meff < N
+
+
 def test_seq_weights_config2_sampled_rows(bm, orc):
     N, L = 50000, 256
     X = synth.clustered_msa(N, L, 21, 12, n_ancestors=5000)
