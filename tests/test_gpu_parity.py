@@ -198,6 +198,31 @@ def test_gibbs_long_sequences_teacher_forced(bm, orc, L, M, engine):
             assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
 
 
+@pytest.mark.parametrize("L,q,M", [(900, 10, 160), (600, 16, 2000), (300, 32, 1500), (777, 21, 333)])
+@pytest.mark.parametrize("engine", ["mma", "mma_pair"])
+def test_gibbs_tensor_core_grid_teacher_forced(bm, orc, L, q, M, engine):
+    """Tensor-core forms across alphabets (block sizes 12, 8, 4, 6 sites),
+    long sequences, ragged chain counts: two sweeps, every site of sampled
+    chains is the oracle's teacher-forced draw."""
+    h, J = synth.planted_local_model(L, q, 17, sigma_h=1.0, sigma_J=0.3)
+    m = load(bm, h, J, engine)
+    c = bm.bm_chains_init(m, M, 41)
+    s0 = states_of(bm, c)
+    bm.bm_gibbs_sweep(m, c, 2, 1.0)
+    bm.bm_device_status(m)
+    s2 = states_of(bm, c)
+    # the intermediate states: replay the first sweep on a copy of the chains
+    c1 = bm.bm_chains_init(m, M, 41)
+    bm.bm_gibbs_sweep(m, c1, 1, 1.0)
+    s1 = states_of(bm, c1)
+    h64, J64 = h.astype(np.float64), J.astype(np.float64)
+    sample = sorted(set(np.random.default_rng(3).choice(M, min(M, 14), replace=False).tolist()) | {0, M - 1})
+    for k in sample:
+        for sw, (a, b) in enumerate([(s0, s1), (s1, s2)]):
+            bad, worst, _ = orc.gibbs_verify(h64, J64, a[k:k + 1], b[k:k + 1], 41, sw, 1.0, k)
+            assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
+
+
 @pytest.mark.parametrize("engine", ["mma", "mma_pair"])
 def test_gibbs_more_chains_than_one_wave(bm, orc, engine):
     """M = 12000 chains: more CTAs (clusters) than the GPU runs at once, so
