@@ -67,9 +67,11 @@ enum { BM_HOST = 0, BM_DEVICE = 1 };
 /* Which kernel form bm_gibbs_sweep uses (bm_model_set_engine). */
 enum {
     BM_ENGINE_SIMT = 0,  /* FP32 CUDA-core gather of J rows */
-    BM_ENGINE_AUTO = 1,  /* default: tensor cores when q >= 10 and the shape fits (the
-                            two-CTA form when it fits, else the one-CTA form), else CUDA
-                            cores (the measured faster form on each side of the crossover) */
+    BM_ENGINE_AUTO = 1,  /* default: tensor cores when q >= 10 and the shape fits, else CUDA
+                            cores; among the tensor-core forms the two-CTA one for long
+                            block pairs (L*q^2 >= 98000 with more than 96 chains per cluster,
+                            >= 63000 otherwise) when it needs no more waves of CTAs (the
+                            measured faster form on each side of each crossover) */
     BM_ENGINE_MMA = 2,   /* tensor cores: one-hot x (fp16 hi + fp16 lo) J, FP32 accumulate;
                             one CTA per SM computes both blocks of a block pair */
     BM_ENGINE_MMA_PAIR = 3  /* the same arithmetic split over the two CTAs of a cluster: each

@@ -363,16 +363,22 @@ int bm_sweep_form(const bm_model_s *m, int M)
     // AUTO: the tensor-core sweep from q = 10 up (measured crossover between
     // q = 8 and q = 12 at L = 256: the one-hot contraction does q times the
     // gather's arithmetic and small alphabets make long sequential blocks);
-    // the two-CTA form (half the coupling bytes per SM) unless it needs more
-    // waves of CTAs than the one-CTA form (long sequences leave room for
-    // fewer chains per CTA).
+    // the two-CTA form (half the coupling bytes per SM) when it needs no more
+    // waves of CTAs than the one-CTA form and the block pairs are long enough
+    // for the MMAs, not the two redraws per pair, to set the pace: the MMA
+    // work of a pair grows as L*q^2 against the redraws, and redraws are
+    // slower with many chains per cluster (measured at q = 21: two-CTA ahead
+    // from L = 240 at 144 chains per cluster, from L = 160 at <= 32).
     if (m->q < 10) return 0;
     const int nc1 = bm_gibbs_mma_chains_per_cta(m, M);
     const int w2 = bm_gibbs_pair_waves(m, M);
     if (nc1 == 0) return w2 > 0 ? 2 : 0;
+    if (w2 == 0) return 1;
     const int nsm = m->num_sms > 0 ? m->num_sms : 1;
     const int w1 = ((M + nc1 - 1) / nc1 + nsm - 1) / nsm;
-    return (w2 > 0 && w2 <= w1) ? 2 : 1;
+    const long long lq2 = (long long)m->L * m->q * m->q;
+    const long long need = bm_gibbs_pair_chains_per_cluster(m, M) > 96 ? 98000 : 63000;
+    return (w2 <= w1 && lq2 >= need) ? 2 : 1;
 }
 
 int bm_sweep_run(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)

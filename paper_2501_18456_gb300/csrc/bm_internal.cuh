@@ -184,6 +184,8 @@ int bm_launch_energy_gather(const float *h, const float *J, int L, int q, const 
 int bm_launch_energy_staged(const bm_model_s *m, const uint8_t *seqs, int n, float *E, int *bad, cudaStream_t st);
 int bm_split_prepare(bm_model_s *m, int bf16, cudaStream_t st);
 int bm_split_block_sites(int L, int q);
+// The in-block coupling layout Jc of the live J (rebuilt when stale).
+int bm_corr_prepare(bm_model_s *m, cudaStream_t st);
 int bm_launch_fields_simt(const bm_model_s *m, const uint8_t *seqs, int n, float *H, cudaStream_t st);
 int bm_launch_fields_tc(bm_model_s *m, const uint8_t *seqs, int n, float *H, int bf16, cudaStream_t st);
 int bm_launch_mutant_scan(const float *h, const float *J, int L, int q, const uint8_t *wt,

@@ -76,7 +76,6 @@ constexpr int kKC = 64;                // fp16 K elements per chunk (128-byte ro
 constexpr int kRowsA = 128;            // MMA M
 constexpr int kTileA = kRowsA * 128;   // bytes of one hi or lo tile (16 KB)
 constexpr int kSlotA = 4 * kTileA;     // ring slot: [hi, lo][block 0, block 1] tiles
-constexpr int kQmax = 32;              // largest alphabet
 constexpr int kThreads = 320;          // 10 warps
 constexpr int kBmax = 32;              // max sites per block
 constexpr int kNBars = 2 * kNA + 2 * kNB + 4 + 4 + 2 + 1;
@@ -222,11 +221,11 @@ __device__ __forceinline__ uint32_t noswz_off(int r, int p)
 
 struct MmaArgs {
     const float *h;
-    const float *Jg;  // gather layout (in-block corrections): Jg[i][j][b][a], block stride bs
+    const float *Jc;  // in-block coupling blocks: [site block][pair slot][b][a padded to q4]
     uint8_t *states;
     int *err;
     uint64_t seed, sweep0, chain0;  // chain0: global index of chain 0 (Philox counter)
-    float beta;
+    float beta_l2e;  // beta * log2(e): weights exp(beta H) = 2^(beta log2(e) H)
     int M, L, q, Lp, bs, B, nb, nK, X, NC, nsweeps;
     long long nblocks;
     uint32_t tmem_cols, acc_stride;  // TMEM columns allocated; columns per accumulator
@@ -237,22 +236,27 @@ struct MmaArgs {
 // hit different banks.
 __host__ __device__ inline int st_stride(int Lp) { return Lp + 4; }
 __host__ __device__ inline int snap_stride(int B) { return 4 * (((B + 3) / 4) | 1); }
+__host__ __device__ inline int q4_of(int q) { return (q + 3) & ~3; }
+// Row stride (floats) of the staged fields, one row per chain: q rounded up
+// to 4, plus 4 when that is an even number of 16-byte units, so that eight
+// consecutive rows start in eight different 16-byte bank groups.
+__host__ __device__ inline int hs_stride(int q) { return ((q4_of(q) >> 2) & 1) ? q4_of(q) : q4_of(q) + 4; }
 
 // Shared-memory carve-up (offsets from the 1024-aligned base).
 struct Smem {
     uint32_t a, b, hs, st, snap, corr, hrow, jtab, bars, misc, total;
 };
 
-__host__ __device__ inline Smem smem_layout(int NC, int Lp, int B, int bs, int nK)
+__host__ __device__ inline Smem smem_layout(int NC, int Lp, int B, int q, int nK)
 {
     Smem s;
     s.a = 0;                                      // slot: hi tiles at +0, +kTileA; lo at +2, +3 kTileA
     s.b = s.a + kNA * kSlotA;
     s.hs = s.b + kNB * NC * 128;
-    s.st = s.hs + kQmax * (NC + 1) * 4;           // fields of one site: [a][chain]
+    s.st = s.hs + NC * hs_stride(q) * 4;          // fields h + G of one site: [chain][a]
     s.snap = s.st + NC * st_stride(Lp);           // [2 pair slots][2 blocks][NC][snap_stride]
     s.corr = (s.snap + 4 * NC * snap_stride(B) + 15) & ~15u;
-    s.hrow = s.corr + (uint32_t)(B * (B - 1) / 2) * bs * 4;  // staged J_ij blocks, j < i in the block
+    s.hrow = s.corr + (uint32_t)(B * (B - 1) / 2) * q * q4_of(q) * 4;  // staged J_ij blocks, j < i in the block
     s.jtab = s.hrow + kRowsA * 4;                 // block's h rows
     s.bars = (s.jtab + nK * 4 + 15) & ~15u;       // first/last site of each K chunk
     s.misc = s.bars + kNBars * 8;
@@ -354,11 +358,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = su32(smem_raw);
     unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    const Smem lay = smem_layout(p.NC, p.Lp, p.B, p.bs, p.nK);
+    const Smem lay = smem_layout(p.NC, p.Lp, p.B, p.q, p.nK);
     float *Hs = reinterpret_cast<float *>(base + lay.hs);
     uint8_t *st = base + lay.st;
     uint8_t *snap = base + lay.snap;
-    const float *corr = reinterpret_cast<const float *>(base + lay.corr);
+    const float4 *corr4 = reinterpret_cast<const float4 *>(base + lay.corr);
     float *hrow = reinterpret_cast<float *>(base + lay.hrow);
     unsigned short *jtab = reinterpret_cast<unsigned short *>(base + lay.jtab);
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + lay.bars);
@@ -431,15 +435,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
 
     // Stage the coupling blocks J_ij (i, j in block kb, j < i) for the
     // in-block corrections: one bulk copy per block of bs floats.
+    // Stage the in-block coupling blocks of block kb (its pairs pi > pj are
+    // the first Bk(Bk-1)/2 slots of its Jc entry): one bulk copy.
     auto stage_corr = [&](long long kb) {
         const Blk g = blk_of(p, kb);
-        const uint32_t bytes = (uint32_t)(g.Bk * (g.Bk - 1) / 2) * (uint32_t)p.bs * 4u;
+        const uint32_t row = (uint32_t)q * (uint32_t)q4_of(q);
+        const uint32_t bytes = (uint32_t)(g.Bk * (g.Bk - 1) / 2) * row * 4u;
         mbar_expect_tx(corr_bar, bytes);
-        int slot = 0;
-        for (int pi = 1; pi < g.Bk; ++pi)
-            for (int pj = 0; pj < pi; ++pj, ++slot)
-                bulk_g2s(su32(base + lay.corr) + (uint32_t)slot * p.bs * 4u,
-                         p.Jg + ((size_t)(g.i0 + pi) * L + (g.i0 + pj)) * p.bs, (uint32_t)p.bs * 4u, corr_bar);
+        if (bytes > 0)
+            bulk_g2s(su32(base + lay.corr), p.Jc + (size_t)(kb % p.nb) * (p.B * (p.B - 1) / 2) * row, bytes,
+                     corr_bar);
     };
 
     if (warp == 0) {
@@ -549,8 +554,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
         const int w = tid - 64;            // 0..127
         const int lane_base = 32 * (warp & 3);
         const int row = lane_base + lane;  // TMEM lane / accumulator row read in the epilogue
-        const unsigned HsStride = (unsigned)NC + 1;
-        const uint32_t blkb = (uint32_t)p.bs;  // staged block stride (floats)
+        const int HS = hs_stride(q), qv = q4_of(q) >> 2;  // float4s per padded row
         bool ok = true;
         long long staged = 0;  // number of correction stagings issued (by w == 0)
         if (w == 0 && nblocks > 0) {
@@ -570,16 +574,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
             const uint8_t *old = snap_of(kb);
             const uint32_t tacc = tmem + ((uint32_t)lane_base << 16) + (uint32_t)slot * p.acc_stride;
             for (int pp = 0; pp < g.Bk && ok; ++pp) {
-                // accumulator rows [pp*q, pp*q + q) of the warps whose lanes hold them -> Hs[a][chain]
+                // accumulator rows [pp*q, pp*q + q) of the warps whose lanes hold them,
+                // plus h, -> Hs[chain][a]
                 const int r0 = pp * q;
                 if (lane_base < r0 + q && lane_base + 32 > r0) {
+                    const bool mine = row >= r0 && row < r0 + q;
+                    const float hv = mine ? hrow[row] : 0.0f;
                     for (int c0 = 0; c0 < NC; c0 += 16) {
                         uint32_t v[16];
                         tmem_ld16(tacc + (uint32_t)c0, v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (row >= r0 && row < r0 + q) {
+                        if (mine) {
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) Hs[(row - r0) * HsStride + c0 + e] = __uint_as_float(v[e]);
+                            for (int e = 0; e < 16; ++e) Hs[(c0 + e) * HS + (row - r0)] = hv + __uint_as_float(v[e]);
                         }
                     }
                 }
@@ -587,34 +594,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                 const int i = g.i0 + pp;
                 for (int ch = w; ch < NC; ch += 128) {
                     const uint64_t m = p.chain0 + cta0 + ch;  // global chain index
+                    // the uniform first: it does not depend on the states
+                    const uint32_t r24 = bm_u24(p.seed, m, sweep, (uint64_t)i, 0);
                     float H[32];
+                    const float4 *hs4 = reinterpret_cast<const float4 *>(Hs + ch * HS);
 #pragma unroll
-                    for (int a = 0; a < 32; ++a)
-                        if (a < q) H[a] = hrow[pp * q + a] + Hs[a * HsStride + ch];
-                    const float *cb = corr + (uint32_t)(pp * (pp - 1) / 2) * blkb;  // blocks (i, j < i)
+                    for (int a4 = 0; a4 < 8; ++a4)
+                        if (a4 < qv) {
+                            const float4 t = hs4[a4];
+                            H[4 * a4] = t.x;
+                            H[4 * a4 + 1] = t.y;
+                            H[4 * a4 + 2] = t.z;
+                            H[4 * a4 + 3] = t.w;
+                        }
+                    // sites jj < pp of the block redrawn since the MMAs: + J_ij(., new) - J_ij(., old)
+                    const float4 *cb = corr4 + (size_t)(pp * (pp - 1) / 2) * q * qv;
                     for (int jj = 0; jj < pp; ++jj) {
                         const int sn = st[ch * Sst + g.i0 + jj], so = old[ch * Ssn + jj];
                         if (sn == so) continue;
-                        const float *rn = cb + jj * blkb + sn * q, *ro = cb + jj * blkb + so * q;
+                        const float4 *rn = cb + (jj * q + sn) * qv, *ro = cb + (jj * q + so) * qv;
 #pragma unroll
-                        for (int a = 0; a < 32; ++a)
-                            if (a < q) H[a] += rn[a] - ro[a];
+                        for (int a4 = 0; a4 < 8; ++a4)
+                            if (a4 < qv) {
+                                const float4 vn = rn[a4], vo = ro[a4];
+                                H[4 * a4] += vn.x - vo.x;
+                                H[4 * a4 + 1] += vn.y - vo.y;
+                                H[4 * a4 + 2] += vn.z - vo.z;
+                                H[4 * a4 + 3] += vn.w - vo.w;
+                            }
                     }
                     float mx = -INFINITY;
 #pragma unroll
                     for (int a = 0; a < 32; ++a)
                         if (a < q) {
-                            H[a] *= p.beta;
+                            H[a] *= p.beta_l2e;
                             mx = fmaxf(mx, H[a]);
                         }
                     float S = 0.0f;
 #pragma unroll
                     for (int a = 0; a < 32; ++a)
                         if (a < q) {
-                            S += expf(H[a] - mx);
-                            H[a] = S;  // prefix sums
+                            S += exp2f(H[a] - mx);
+                            H[a] = S;  // prefix sums of exp(beta H_a - max_b beta H_b)
                         }
-                    const uint32_t r24 = bm_u24(p.seed, m, sweep, (uint64_t)i, 0);
                     const float thr = ((float)r24 * 5.9604644775390625e-8f) * S;
                     int pick = q - 1;
 #pragma unroll
@@ -852,7 +874,7 @@ int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M)
     const int Lp = (m->L + 15) & ~15;
     const int B = block_sites(m->L, m->q);
     const int nK = (m->L * m->q + kKC - 1) / kKC;
-    while (nc >= 16 && smem_layout(nc, Lp, B, m->bs, nK).total + 1024 > 227 * 1024) nc -= 16;
+    while (nc >= 16 && smem_layout(nc, Lp, B, m->q, nK).total + 1024 > 227 * 1024) nc -= 16;
     return nc >= 16 ? nc : 0;
 }
 
@@ -897,18 +919,19 @@ int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, 
     const int NC = bm_gibbs_mma_chains_per_cta(m, c->M);
     if (NC == 0) return bm_fail(BM_EINVAL, "tensor-core sweep: shape does not fit shared memory");
     {
-        const int rc = bm_split_prepare(m, 0, st);
+        int rc = bm_split_prepare(m, 0, st);
+        if (rc == BM_OK) rc = bm_corr_prepare(m, st);
         if (rc != BM_OK) return rc;
     }
     MmaArgs a;
     a.h = m->h;
-    a.Jg = m->Jg;
+    a.Jc = m->Jc;
     a.states = c->s;
     a.err = m->dflags + 3;
     a.seed = c->seed;
     a.chain0 = c->chain0;
     a.sweep0 = c->sweep;
-    a.beta = beta;
+    a.beta_l2e = (float)((double)beta * 1.4426950408889634);
     a.M = c->M;
     a.L = c->L;
     a.q = c->q;
@@ -923,7 +946,7 @@ int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, 
     a.X = a.nK / 2;  // main chunks before the previous pair's first delta step
     a.acc_stride = NC <= 32 ? 32 : NC <= 64 ? 64 : 128;
     a.tmem_cols = 4 * a.acc_stride;  // four accumulators
-    const Smem lay = smem_layout(NC, a.Lp, a.B, a.bs, a.nK);
+    const Smem lay = smem_layout(NC, a.Lp, a.B, a.q, a.nK);
     const size_t smem = lay.total + 1024;
     BM_CK(cudaFuncSetAttribute(k_gibbs_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (c->M + NC - 1) / NC;

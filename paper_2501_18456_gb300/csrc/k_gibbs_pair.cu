@@ -907,6 +907,11 @@ int model_prepare(bm_model_s *m, cudaStream_t st)
 
 }  // namespace
 
+int bm_corr_prepare(bm_model_s *m, cudaStream_t st)
+{
+    return corr_prepare(m, bm_split_block_sites(m->L, m->q), st);
+}
+
 // Chains per cluster for the two-CTA tensor-core sweep (multiple of 16,
 // <= 160), or 0 when the shape does not fit one CTA's shared memory or L < 2.
 int bm_gibbs_pair_chains_per_cluster(const bm_model_s *m, int M)

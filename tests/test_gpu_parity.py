@@ -597,14 +597,24 @@ def test_shards_reproduce_the_full_ensemble(bm, engine):
 
 
 def test_sweep_engine_resolution(bm):
-    """AUTO resolves to the two-CTA tensor-core form for protein alphabets and
-    to the CUDA-core form for small alphabets; explicit engines are kept."""
-    h, J = synth.planted_local_model(64, 21, 3)
+    """AUTO: the two-CTA tensor-core form for long block pairs, the one-CTA
+    form for short ones, CUDA cores for small alphabets; explicit engines are
+    kept."""
+    h, J = synth.planted_local_model(256, 21, 3)
     m = load(bm, h, J)
     assert bm.bm_model_sweep_engine(m, 10000) == bm.BM_ENGINE_MMA_PAIR
     assert bm.bm_model_sweep_engine(m, 1) == bm.BM_ENGINE_MMA_PAIR
     bm.bm_model_set_engine(m, bm.BM_ENGINE_MMA)
     assert bm.bm_model_sweep_engine(m, 10000) == bm.BM_ENGINE_MMA
+    # short block pairs: the two redraws per pair set the pace, one CTA is faster
+    hs, Js = synth.planted_local_model(120, 21, 3)
+    ms = load(bm, hs, Js)
+    assert bm.bm_model_sweep_engine(ms, 10000) == bm.BM_ENGINE_MMA
+    assert bm.bm_model_sweep_engine(ms, 1024) == bm.BM_ENGINE_MMA
+    hm, Jm = synth.planted_local_model(200, 21, 3)
+    mm = load(bm, hm, Jm)
+    assert bm.bm_model_sweep_engine(mm, 10000) == bm.BM_ENGINE_MMA
+    assert bm.bm_model_sweep_engine(mm, 1024) == bm.BM_ENGINE_MMA_PAIR
     h5, J5 = synth.planted_local_model(64, 5, 3)
     m5 = load(bm, h5, J5)
     assert bm.bm_model_sweep_engine(m5, 10000) == bm.BM_ENGINE_SIMT
