@@ -67,11 +67,13 @@ enum { BM_HOST = 0, BM_DEVICE = 1 };
 /* Which kernel form bm_gibbs_sweep uses (bm_model_set_engine). */
 enum {
     BM_ENGINE_SIMT = 0,  /* FP32 CUDA-core gather of J rows */
-    BM_ENGINE_AUTO = 1,  /* default: tensor cores when q >= 10 and the shape fits, else CUDA
-                            cores; among the tensor-core forms the two-CTA one for long
-                            block pairs (L*q^2 >= 98000 with more than 96 chains per cluster,
-                            >= 63000 otherwise) when it needs no more waves of CTAs (the
-                            measured faster form on each side of each crossover) */
+    BM_ENGINE_AUTO = 1,  /* default: the measured faster form.  Tensor cores when
+                            M*L^2 >= T(q) and L >= L0(q) (q >= 16: 2e7, 48; q 10-15: 5e7,
+                            100; q 8-9: 2.5e8, 120; q 5-7: 5e8, 180; q 2-4: 5e7, 150) and
+                            the shape fits, else CUDA cores.  Among the tensor-core forms
+                            the two-CTA one for long block pairs (L*q^2 >= 98000 with more
+                            than 96 chains per cluster, >= 63000 otherwise) when it needs
+                            no more waves of CTAs than the one-CTA form. */
     BM_ENGINE_MMA = 2,   /* tensor cores: one-hot x (fp16 hi + fp16 lo) J, FP32 accumulate;
                             one CTA per SM computes both blocks of a block pair */
     BM_ENGINE_MMA_PAIR = 3  /* the same arithmetic split over the two CTAs of a cluster: each
@@ -329,8 +331,8 @@ int bm_fields(bm_model m, const uint8_t *seqs_dev, int n, float *H_dev, int form
  * models on one GPU).  A batch groups (model, chains) pairs with the same q;
  * bm_batch_sweep runs nsweeps sweeps of every pair in ONE launch over a work
  * list of chain tiles, longest models first.  Two forms:
- *  - tensor cores, when every model's engine resolves to a tensor-core form
- *    (bm_model_sweep_engine) and every model fits: the two-CTA sweep, one
+ *  - tensor cores, when q >= 10, no model's engine is BM_ENGINE_SIMT and
+ *    every model fits: the two-CTA sweep, one
  *    cluster per (model, tile), each cluster reading its model's arguments
  *    and TMA descriptor from the list (refreshed from host memory by each
  *    call); the arithmetic per chain is that of BM_ENGINE_MMA_PAIR;

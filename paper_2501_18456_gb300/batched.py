@@ -7,8 +7,8 @@ M = 2048 chains each, planted local models (h ~ N(0, 0.5^2), J ~ N(0,
 site-updates/s of (a) the batched launch in the default (tensor-core) form,
 autotuned, (b) the batched launch in the CUDA-core form (graph replay,
 autotuned), (c) 64 sequential launches of the plain FP32 CUDA-core sweep,
-(d) 64 sequential launches with the default engine (tensor cores where
-q >= 10).
+(d) 64 sequential launches with the default engine (AUTO: the measured
+faster form per model).
 
 This module only builds inputs and times the library's entry points.
 """

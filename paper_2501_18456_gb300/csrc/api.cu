@@ -355,21 +355,36 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
 
 }  // extern "C"
 
+// AUTO: do the tensor-core forms beat the CUDA-core gather for this shape?
+// Measured on an L x q x M grid (L 48-256, q 4-21, M 1000-20000): the
+// tensor-core forms redraw the sites of a block one after another, which
+// puts a floor of a few microseconds per site under a sweep, so small
+// problems (short L, few chains) go to the gather; the gather's efficiency
+// also depends on q (alphabets of 5-7 symbols suit its lane layout best).
+// Rule: tensor cores when M*L^2 >= T(q) and L >= L0(q).
+static bool tensor_beats_gather(int L, int q, int M)
+{
+    const double work = (double)M * L * L;
+    if (q >= 16) return work >= 2e7 && L >= 48;
+    if (q >= 10) return work >= 5e7 && L >= 100;
+    if (q >= 8) return work >= 2.5e8 && L >= 120;
+    if (q >= 5) return work >= 5e8 && L >= 180;
+    if (q >= 2) return work >= 5e7 && L >= 150;
+    return false;
+}
+
 int bm_sweep_form(const bm_model_s *m, int M)
 {
     if (m->engine == BM_ENGINE_MMA_PAIR) return 2;
     if (m->engine == BM_ENGINE_MMA) return 1;
     if (m->engine != BM_ENGINE_AUTO) return 0;
-    // AUTO: the tensor-core sweep from q = 10 up (measured crossover between
-    // q = 8 and q = 12 at L = 256: the one-hot contraction does q times the
-    // gather's arithmetic and small alphabets make long sequential blocks);
+    if (!tensor_beats_gather(m->L, m->q, M)) return 0;
     // the two-CTA form (half the coupling bytes per SM) when it needs no more
     // waves of CTAs than the one-CTA form and the block pairs are long enough
     // for the MMAs, not the two redraws per pair, to set the pace: the MMA
     // work of a pair grows as L*q^2 against the redraws, and redraws are
     // slower with many chains per cluster (measured at q = 21: two-CTA ahead
     // from L = 240 at 144 chains per cluster, from L = 160 at <= 32).
-    if (m->q < 10) return 0;
     const int nc1 = bm_gibbs_mma_chains_per_cta(m, M);
     const int w2 = bm_gibbs_pair_waves(m, M);
     if (nc1 == 0) return w2 > 0 ? 2 : 0;

@@ -671,9 +671,12 @@ int bm_batch_create(const bm_model *models, const bm_chains *chains, int count, 
         b->Lmax = std::max(b->Lmax, m->L);
         b->nsm = m->num_sms > 0 ? m->num_sms : 1;
     }
-    // tensor-core form when every model's engine resolves to the tensor cores
-    bool tc = true;
-    for (int k = 0; k < count; ++k) tc = tc && bm_sweep_form(b->models[k], b->chains[k]->M) != 0;
+    // tensor-core form when no model is held to the CUDA cores and q >= 10 (a
+    // batch packs every model's tiles into one launch, so the per-model
+    // small-problem rule of AUTO does not apply; below q = 10 the gather's
+    // batch is kept)
+    bool tc = b->q >= 10;
+    for (int k = 0; k < count; ++k) tc = tc && b->models[k]->engine != BM_ENGINE_SIMT;
     if (tc && bm_pair_batch_create(b->models.data(), b->chains.data(), count, &b->pair) == BM_OK) {
         *out = b;
         return BM_OK;

@@ -851,11 +851,17 @@ int make_map(CUtensorMap *map, const void *ptr, int rows, int Kp, int box_rows, 
 }
 
 // Sites per block: as many as fill the 128 accumulator rows (at most kBmax),
-// but at least two blocks per sweep, so that the two blocks of a pair never
-// hold the same sites.
+// as long as the block's in-block coupling blocks (B(B-1)/2 of them, q rows
+// of q rounded up to 4 floats, staged in shared memory by the sweeps) fit
+// 32 KB, and at least two blocks per sweep, so that the two blocks of a pair
+// never hold the same sites.  (Without the 32 KB cap, alphabets of 5 or 6
+// symbols would stage 40-48 KB and leave room for too few chains per CTA.)
 int block_sites(int L, int q)
 {
+    constexpr long long kCorrBudget = 32768;
+    const long long row_bytes = (long long)q * ((q + 3) & ~3) * 4;
     int B = std::min(kBmax, kRowsA / q);
+    while (B > 2 && (long long)B * (B - 1) / 2 * row_bytes > kCorrBudget) --B;
     if ((L + B - 1) / B < 2) B = (L + 1) / 2;
     return B;
 }

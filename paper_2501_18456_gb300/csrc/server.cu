@@ -255,14 +255,19 @@ int bm_server_destroy(bm_server s)
 int bm_server_add_model(bm_server s, bm_model m, int *id)
 {
     if (!s || !m || !id) return bm_fail(BM_EINVAL, "bm_server_add_model: NULL argument");
-    // the tensor-core layout is built here, once, so no request rebuilds it
+    // The tensor-core layouts (split J, in-block corrections) are built here,
+    // once and synchronously: requests run on different streams, so a layout
+    // built lazily by one request could be read by a concurrent one before
+    // its build kernel ran.  Built for every model a tensor-core form could
+    // serve (AUTO's choice depends on each request's chain count).
     cudaStream_t st = nullptr;
     BM_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     int rc = BM_OK;
-    const bool mma = m->engine == BM_ENGINE_MMA || m->engine == BM_ENGINE_MMA_PAIR ||
-                     (m->engine == BM_ENGINE_AUTO && m->q >= 10);
-    if (mma && (bm_gibbs_mma_chains_per_cta(m, 1) > 0 || bm_gibbs_pair_chains_per_cluster(m, 1) > 0))
+    const bool tc = m->engine != BM_ENGINE_SIMT && m->q >= 2;
+    if (tc && (bm_gibbs_mma_chains_per_cta(m, 1) > 0 || bm_gibbs_pair_chains_per_cluster(m, 1) > 0)) {
         rc = bm_split_prepare(m, 0, st);
+        if (rc == BM_OK) rc = bm_corr_prepare(m, st);
+    }
     const cudaError_t e = cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     if (rc != BM_OK) return rc;

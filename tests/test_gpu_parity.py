@@ -597,20 +597,22 @@ def test_shards_reproduce_the_full_ensemble(bm, engine):
 
 
 def test_sweep_engine_resolution(bm):
-    """AUTO: the two-CTA tensor-core form for long block pairs, the one-CTA
-    form for short ones, CUDA cores for small alphabets; explicit engines are
-    kept."""
+    """AUTO: CUDA cores for small problems, the tensor cores for large ones
+    (thresholds by alphabet size), and among those the two-CTA form for long
+    block pairs, the one-CTA form for short ones; explicit engines are kept."""
     h, J = synth.planted_local_model(256, 21, 3)
     m = load(bm, h, J)
     assert bm.bm_model_sweep_engine(m, 10000) == bm.BM_ENGINE_MMA_PAIR
-    assert bm.bm_model_sweep_engine(m, 1) == bm.BM_ENGINE_MMA_PAIR
+    assert bm.bm_model_sweep_engine(m, 1024) == bm.BM_ENGINE_MMA_PAIR
+    assert bm.bm_model_sweep_engine(m, 1) == bm.BM_ENGINE_SIMT  # one chain: a small problem
     bm.bm_model_set_engine(m, bm.BM_ENGINE_MMA)
+    assert bm.bm_model_sweep_engine(m, 1) == bm.BM_ENGINE_MMA
     assert bm.bm_model_sweep_engine(m, 10000) == bm.BM_ENGINE_MMA
     # short block pairs: the two redraws per pair set the pace, one CTA is faster
     hs, Js = synth.planted_local_model(120, 21, 3)
     ms = load(bm, hs, Js)
     assert bm.bm_model_sweep_engine(ms, 10000) == bm.BM_ENGINE_MMA
-    assert bm.bm_model_sweep_engine(ms, 1024) == bm.BM_ENGINE_MMA
+    assert bm.bm_model_sweep_engine(ms, 1024) == bm.BM_ENGINE_SIMT  # M*L^2 below 2e7 at q = 21
     hm, Jm = synth.planted_local_model(200, 21, 3)
     mm = load(bm, hm, Jm)
     assert bm.bm_model_sweep_engine(mm, 10000) == bm.BM_ENGINE_MMA
@@ -618,6 +620,17 @@ def test_sweep_engine_resolution(bm):
     h5, J5 = synth.planted_local_model(64, 5, 3)
     m5 = load(bm, h5, J5)
     assert bm.bm_model_sweep_engine(m5, 10000) == bm.BM_ENGINE_SIMT
+    # small problems go to the gather; large small-alphabet ones to the tensor cores
+    h48, J48 = synth.planted_local_model(48, 21, 3)
+    assert bm.bm_model_sweep_engine(load(bm, h48, J48), 1000) == bm.BM_ENGINE_SIMT
+    h4, J4 = synth.planted_local_model(256, 4, 3)
+    m4 = load(bm, h4, J4)
+    assert bm.bm_model_sweep_engine(m4, 5000) == bm.BM_ENGINE_MMA
+    assert bm.bm_model_sweep_engine(m4, 500) == bm.BM_ENGINE_SIMT
+    h6, J6 = synth.planted_local_model(256, 5, 3)
+    m6 = load(bm, h6, J6)
+    assert bm.bm_model_sweep_engine(m6, 20000) == bm.BM_ENGINE_MMA
+    assert bm.bm_model_sweep_engine(m6, 5000) == bm.BM_ENGINE_SIMT
     with pytest.raises(bm.BmError) as e:
         bm.bm_model_sweep_engine(m5, 0)
     assert e.value.code == bm.BM_EINVAL
