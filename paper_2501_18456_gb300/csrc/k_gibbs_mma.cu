@@ -60,6 +60,7 @@
 // its loop, the producer waits (bounded) for its own copies, TMEM is
 // released and the chains are left unchanged.
 #include "bm_internal.cuh"
+#include "tc_common.cuh"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -67,6 +68,8 @@
 
 #include <algorithm>
 #include <mutex>
+
+using namespace bmtc;
 
 namespace {
 
@@ -79,146 +82,6 @@ constexpr int kSlotA = 4 * kTileA;     // ring slot: [hi, lo][block 0, block 1] 
 constexpr int kThreads = 320;          // 10 warps
 constexpr int kBmax = 32;              // max sites per block
 constexpr int kNBars = 2 * kNA + 2 * kNB + 4 + 4 + 2 + 1;
-constexpr uint64_t kWaitNs = 2000000000ull;
-
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
-{
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtimer() - t0 > kWaitNs) {
-            *abort_flag = 1;
-            atomicOr(err, 4);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
-// tcgen05 matrix descriptors (K-major).  Bits: start >> 4 [0,14), leading
-// byte offset >> 4 [16,30), stride byte offset >> 4 [32,46), fixed 0b001 at
-// [46,49), layout type [61,64) (0 = no swizzle, 2 = 128B swizzle).
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
-{
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;            // leading offset (unused for 128B swizzle K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;  // 8-row groups 1024 bytes apart
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-__device__ __forceinline__ uint64_t desc_noswz(uint32_t saddr)
-{
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(128 >> 4) << 16;   // K-adjacent core matrices 128 bytes apart
-    d |= (uint64_t)(1024 >> 4) << 32;  // 8-row groups 1024 bytes apart
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void named_bar(int id, int n)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
-// Named barrier returning the OR of `pred` over its n threads (the same
-// answer in every participant).
-__device__ __forceinline__ bool named_bar_or(int id, int n, bool pred)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "barrier.cta.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(id), "r"(n)
-        : "memory");
-    return r != 0;
-}
-
-// Byte offset of 16-byte piece p of row r in a no-swizzle K-major tile with
-// 8 pieces per row: core matrix (r/8, p) at ((r/8)*8 + p)*128, row r%8 at +16*(r%8).
-__device__ __forceinline__ uint32_t noswz_off(int r, int p)
-{
-    return (uint32_t)((((r >> 3) << 3) + p) << 7) + (uint32_t)((r & 7) << 4);
-}
-
 struct MmaArgs {
     const float *h;
     const float *Jc;  // in-block coupling blocks: [site block][pair slot][b][a padded to q4]
@@ -590,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                         }
                     }
                 }
-                named_bar(1, 128);
+                named_bar_sync(1, 128);
                 const int i = g.i0 + pp;
                 for (int ch = w; ch < NC; ch += 128) {
                     const uint64_t m = p.chain0 + cta0 + ch;  // global chain index
@@ -644,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                         if (a < q && thr < H[a]) pick = a;
                     st[ch * Sst + i] = (uint8_t)pick;
                 }
-                named_bar(1, 128);  // Hs is rewritten for the next site
+                named_bar_sync(1, 128);  // Hs is rewritten for the next site
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -659,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gibbs_mma(const __grid_constant
                         sn[ch * Ssn + x] = st[ch * Sst + gn.i0 + x];
                     }
                 }
-            named_bar(1, 128);
+            named_bar_sync(1, 128);
             // the staged blocks are free again: stage the next block's
             if (w == 0 && ok && !*abort_flag && kb + 1 < nblocks) {
                 stage_corr(kb + 1);

@@ -151,34 +151,6 @@ __device__ __forceinline__ void cluster_sync_all()
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
-// ---------------------------------------------------------------- tcgen05 helpers
-// K-major no-swizzle descriptor: K-adjacent core matrices 128 bytes apart,
-// 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t desc_noswz(uint32_t saddr)
-{
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(128 >> 4) << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
-
-// Byte offset of 16-byte piece p of row r in a no-swizzle K-major tile with
-// 8 pieces per row.
-__device__ __forceinline__ uint32_t noswz_off(int r, int p)
-{
-    return (uint32_t)((((r >> 3) << 3) + p) << 7) + (uint32_t)((r & 7) << 4);
-}
-
 struct PairArgs {
     const float *h;
     const float *Jc;  // in-block coupling blocks: [site block][pair slot][b][a padded to q4]

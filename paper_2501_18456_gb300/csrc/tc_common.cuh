@@ -137,6 +137,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// K-major no-swizzle matrix descriptor: K-adjacent core matrices 128 bytes
+// apart, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_noswz(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Byte offset of 16-byte piece p of row r in a no-swizzle K-major tile with
+// 8 pieces per row: core matrix (r/8, p) at ((r/8)*8 + p)*128, row r%8 at +16*(r%8).
+__device__ __forceinline__ uint32_t noswz_off(int r, int p)
+{
+    return (uint32_t)((((r >> 3) << 3) + p) << 7) + (uint32_t)((r & 7) << 4);
+}
+
+// 16 consecutive TMEM columns of the warp's 32 lanes (one lane per thread);
+// the caller waits with tcgen05.wait::ld before using v.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
 // Named barrier over n threads of the CTA.
 __device__ __forceinline__ void named_bar_sync(int id, int n)
 {
