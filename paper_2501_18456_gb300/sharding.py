@@ -8,9 +8,9 @@ the int32 pair counts before the update (exact); every rank then applies the
 same deterministic bm_update with the total chain count, so the replicas'
 parameters stay identical.
 
-On the GPU machines of this build each run has one GPU, so bench.py runs
-independent replicas; these helpers and their world-size-2 tests on CPU
-(gloo) cover the sharded path.
+bench.py --gpus N runs N independent replicas (weak scaling, no collective
+on the data path); these helpers give the sharded alternative, with the one
+all-reduce above, and are exercised by world-size-2 gloo runs on CPU.
 """
 from __future__ import annotations
 
