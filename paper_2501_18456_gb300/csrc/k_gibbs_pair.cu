@@ -3,8 +3,9 @@
 //
 // Method: Sec. 2.1 ("Monte Carlo estimation of the gradient"), sweep = every
 // site once in order (Sec. 3.3).  The arithmetic is that of the single-CTA
-// tensor-core sweep (k_gibbs_mma.cu): sites in blocks of B = floor(128/q),
-// the fields of a block's 128 rows (i,a) as the contraction of the coupling
+// tensor-core sweep (k_gibbs_mma.cu): sites in blocks of B <= floor(128/q)
+// (bm_split_block_sites), the fields of a block's 128 rows (i,a) as the
+// contraction of the coupling
 // rows (fp16 hi + fp16 lo, FP32 accumulation in TMEM) with the one-hot
 // states, then an exact sequential redraw of the block's sites with in-block
 // corrections, blocks taken in pairs (2P, 2P+1).
@@ -23,8 +24,8 @@
 // arrives on the peer's ready barrier of that block's parity with release
 // semantics at cluster scope; waiters acquire at cluster scope.  CTA 0 makes
 // that copy of block 2P only once CTA 1's generators have finished pair P's
-// main chunks (gen_done), which read block 2P's pre-redraw states.  Schedule of pair P in
-// CTA r, each step a run of 64-column K chunks:
+// main chunks (gen_done), which read block 2P's pre-redraw states.
+// Schedule of pair P in CTA r, each step a run of 64-column K chunks:
 //   A  main chunks [0, X) into block 2P+r: states after block 2P-3, with
 //      blocks 2P-2 and 2P-1 (being redrawn) from their pre-redraw snapshots;
 //   B  (CTA 1 only) delta chunks of block 2P-2 (+1 at the new, -1 at the old
@@ -45,14 +46,21 @@
 //   warp 1       TMEM allocation (two accumulators of NC columns, own block
 //                j = kb/2 in slot j % 2) and the single MMA-issuing thread
 //                (M = 128 rows, N = NC chains, K = 16, hi and lo);
-//   warps 2-6    drawers, one thread per chain (warps 2-5 read the four TMEM
-//                lane quarters of a site's rows into shared memory);
+//   warps 2-6    drawers, one thread per chain: warps 2-5 read the four TMEM
+//                lane quarters of a site's rows, add h and store them as one
+//                padded row per chain; each thread reads its row and the
+//                staged in-block coupling blocks (padded layout Jc, one bulk
+//                copy per block) with 128-bit loads, then draws;
 //   warps 7-11   generators of the one-hot operand tiles (2-slot ring), one
 //                thread per chain (zero the row, then store its few nonzeros).
 // Every wait is bounded by %globaltimer (2 s); a timeout sets the CTA's abort
 // flag and bit 2 of the model's device error word.  Both CTAs meet at a
 // cluster barrier before leaving, and the chains are written back only when
 // neither CTA aborted.
+//
+// Batch mode (k_gibbs_pair<true>): cluster k runs work item k of a list,
+// i.e. its own model's arguments, TMA descriptor and chain tile, so many
+// models of uneven length are swept in one launch.
 #include "bm_internal.cuh"
 #include "tc_common.cuh"
 
