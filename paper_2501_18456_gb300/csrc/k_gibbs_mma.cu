@@ -6,8 +6,9 @@
 // H_i(a) = h_i(a) + sum_{j != i} J_ij(a, s_j), a contraction of the
 // coupling rows (i,a) with the one-hot state X[m][(j,b)] = [s_j^m == b].
 //
-// Block-sequential exact Gibbs.  The sites are processed in blocks of B =
-// floor(128/q) consecutive sites (global block counter kb over the launch,
+// Block-sequential exact Gibbs.  The sites are processed in blocks of B <=
+// floor(128/q) consecutive sites (block_sites: the block's in-block coupling
+// blocks must also fit 32 KB of staging; global block counter kb over the launch,
 // block kb covers sites of block kb mod nb of sweep kb / nb).  The MMAs
 // compute, for the 128 rows (i,a) of a block and all the CTA's chains,
 //     G[(i,a), m] = sum_{(j,b)} J_ij(a,b) X[m][(j,b)]
@@ -48,10 +49,11 @@
 //              chains, K = 16 per instruction, hi and lo) and commits each
 //              ring slot back to its producer;
 //   warps 2-5  drawers: per site, read its q accumulator rows (tcgen05.ld,
-//              one TMEM lane = one row (i,a) per thread) into shared memory,
-//              then redraw it, one thread per chain, with the
-//              in-block corrections from coupling blocks staged by bulk
-//              copies; they also take the snapshots;
+//              one TMEM lane = one row (i,a) per thread), add h and store
+//              them as one padded row per chain; then redraw the site, one
+//              thread per chain, reading its row and the in-block coupling
+//              blocks (padded layout Jc, one bulk copy per block) with
+//              128-bit loads; they also take the snapshots;
 //   warps 6-9  generators: build the one-hot operand tile (NC rows x 64 K,
 //              no swizzle) of each K chunk into a 3-slot ring, one thread
 //              per chain.
