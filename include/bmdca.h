@@ -331,7 +331,7 @@ int bm_fields(bm_model m, const uint8_t *seqs_dev, int n, float *H_dev, int form
  * models on one GPU).  A batch groups (model, chains) pairs with the same q;
  * bm_batch_sweep runs nsweeps sweeps of every pair in ONE launch over a work
  * list of chain tiles, longest models first.  Two forms:
- *  - tensor cores, when q >= 10, no model's engine is BM_ENGINE_SIMT and
+ *  - tensor cores, when q >= 2, no model's engine is BM_ENGINE_SIMT and
  *    every model fits: the two-CTA sweep, one
  *    cluster per (model, tile), each cluster reading its model's arguments
  *    and TMA descriptor from the list (refreshed from host memory by each

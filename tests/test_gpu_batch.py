@@ -96,13 +96,13 @@ def test_batch_rejects_mixed_alphabets(bm):
 
 # ---------------------------------------------------------------- tensor-core form
 
-TC_SHAPES = [(256, 700), (37, 300), (512, 500), (90, 1), (150, 2048), (21, 64)]  # (L, M), q = 21
+TC_SHAPES = [(256, 700), (37, 300), (512, 500), (90, 1), (150, 2048), (21, 64)]  # (L, M)
 
 
-def build_tc(bm, seed=0, engine=None):
+def build_tc(bm, seed=0, engine=None, q=21):
     models, chains = [], []
     for k, (L, M) in enumerate(TC_SHAPES):
-        h, J = synth.planted_local_model(L, 21, seed + k, sigma_h=1.0, sigma_J=0.3)
+        h, J = synth.planted_local_model(L, q, seed + k, sigma_h=1.0, sigma_J=0.3)
         m = bm.bm_potts_load(to_dev(h), to_dev(J))
         if engine is not None:
             bm.bm_model_set_engine(m, engine)
@@ -111,12 +111,13 @@ def build_tc(bm, seed=0, engine=None):
     return models, chains
 
 
-def test_tensor_core_batch_matches_oracle_and_per_model_sweeps(bm, orc):
-    """A batch of q=21 models (engines resolving to the tensor cores) runs the
-    two-CTA form over (model, tile) clusters: every sampled chain's sweep is
-    the oracle's teacher-forced draw, and further sweeps equal per-model
-    two-CTA sweeps of the same chains."""
-    mh, chains = build_tc(bm)
+@pytest.mark.parametrize("q", [21, 5])
+def test_tensor_core_batch_matches_oracle_and_per_model_sweeps(bm, orc, q):
+    """A batch of models with default engines runs the two-CTA form over
+    (model, tile) clusters: every sampled chain's sweep is the oracle's
+    teacher-forced draw, and further sweeps equal per-model two-CTA sweeps
+    of the same chains (protein and RNA alphabets)."""
+    mh, chains = build_tc(bm, q=q)
     models = [m for m, _, _ in mh]
     b = bm.Batch(models, chains)
     shp = b.shape()
@@ -134,7 +135,7 @@ def test_tensor_core_batch_matches_oracle_and_per_model_sweeps(bm, orc):
                                              s1[k:k + 1], 200 + TC_SHAPES.index((m.L, c.M)), 0, 1.0, k)
             assert bad == 0 or worst < 1e-5, (m.L, k, bad, worst)
     # continue: batch vs the same chains swept per model
-    ref_mh, ref_c = build_tc(bm, engine=bm.BM_ENGINE_MMA_PAIR)
+    ref_mh, ref_c = build_tc(bm, engine=bm.BM_ENGINE_MMA_PAIR, q=q)
     for (m, _, _), c, s in zip(ref_mh, ref_c, after):
         bm.bm_chains_set(c, to_dev(s))
         bm.bm_chains_set_sweep_counter(c, 1)
