@@ -67,7 +67,10 @@ enum { BM_HOST = 0, BM_DEVICE = 1 };
 /* Which kernel form bm_gibbs_sweep uses (bm_model_set_engine). */
 enum {
     BM_ENGINE_SIMT = 0,  /* FP32 CUDA-core gather of J rows */
-    BM_ENGINE_AUTO = 1,  /* default: the measured faster form.  Tensor cores when
+    BM_ENGINE_AUTO = 1,  /* default: the measured faster form.  The two-CTA form when
+                            4 <= q <= 8, L >= 120, M >= 4096 and a site block's 64-column
+                            K chunks number at most 3x its sites (there it takes its
+                            tensor-memory operand form).  Otherwise tensor cores when
                             M*L^2 >= T(q) and L >= L0(q) (q >= 16: 2e7, 48; q 10-15: 5e7,
                             100; q 8-9: 2.5e8, 120; q 5-7: 5e8, 180; q 2-4: 5e7, 150) and
                             the shape fits, else CUDA cores.  Among the tensor-core forms
@@ -78,7 +81,10 @@ enum {
                             one CTA per SM computes both blocks of a block pair */
     BM_ENGINE_MMA_PAIR = 3  /* the same arithmetic split over the two CTAs of a cluster: each
                                CTA streams and redraws every other site block, the new states
-                               are exchanged through distributed shared memory */
+                               are exchanged through distributed shared memory.  Where a
+                               block's K chunks number at most 4x its sites, the one-hot
+                               states are the MMA's A operand in tensor memory (128 chains
+                               per cluster, one per TMEM lane) and J the B operand */
 };
 
 /* Library version string, e.g. "bmdca-gb300 0.1". */

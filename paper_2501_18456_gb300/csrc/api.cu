@@ -378,6 +378,13 @@ int bm_sweep_form(const bm_model_s *m, int M)
     if (m->engine == BM_ENGINE_MMA_PAIR) return 2;
     if (m->engine == BM_ENGINE_MMA) return 1;
     if (m->engine != BM_ENGINE_AUTO) return 0;
+    // Alphabets of 4-8 symbols with blocks whose K chunks are at most three
+    // times their sites: the two-CTA sweep in its tensor-memory operand form
+    // (measured 1.1-2.0x ahead of the other forms at L 120-500, M 4096-20000;
+    // behind for q = 2, for q = 21 at short L and near 4 chunks per site).
+    if (M >= 4096 && m->L >= 120 && m->q >= 4 && m->q <= 8 && bm_gibbs_pair_tm(m) &&
+        (m->L * m->q + 63) / 64 <= 3 * bm_split_block_sites(m->L, m->q))
+        return 2;
     if (!tensor_beats_gather(m->L, m->q, M)) return 0;
     // the two-CTA form (half the coupling bytes per SM) when it needs no more
     // waves of CTAs than the one-CTA form and the block pairs are long enough

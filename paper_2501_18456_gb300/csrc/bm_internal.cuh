@@ -140,6 +140,7 @@ int bm_gibbs_mma_chains_per_cta(const bm_model_s *m, int M);
 int bm_launch_gibbs_mma(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
 int bm_gibbs_pair_chains_per_cluster(const bm_model_s *m, int M);
 int bm_gibbs_pair_waves(const bm_model_s *m, int M);
+bool bm_gibbs_pair_tm(const bm_model_s *m);
 // Batches of (model, chains) pairs swept by the two-CTA tensor-core kernel
 // in one launch over a work list of chain tiles.
 struct bm_pair_batch_s;

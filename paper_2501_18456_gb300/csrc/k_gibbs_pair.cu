@@ -137,14 +137,28 @@ __device__ __forceinline__ bool mbar_try_cl(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_try_cl_suspend(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait with acquire semantics at cluster scope (barriers that the
-// peer CTA arrives on, or whose arrivals follow data the peer wrote).
+// peer CTA arrives on, or whose arrivals follow data the peer wrote); the
+// waiting thread is suspended between probes, as in mbar_wait.
 __device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
 {
     if (mbar_try_cl(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     for (;;) {
-        if (mbar_try_cl(bar, parity)) return true;
+        if (mbar_try_cl_suspend(bar, parity)) return true;
         if (*abort_flag) return false;
         if (gtimer() - t0 > kWaitNs) {
             *abort_flag = 1;
@@ -167,6 +181,7 @@ struct PairArgs {
     uint64_t seed, sweep0, chain0;
     float beta_l2e;   // beta * log2(e): weights exp(beta H) = 2^(beta log2(e) H)
     int M, L, q, Lp, B, nb, nK, X, NC;
+    int na, nmma;     // tensor-memory operand form: coupling ring slots, MMA N (block rows rounded up to 16)
     long long nblocks;
     uint32_t tmem_cols, acc_stride;
 };
@@ -772,6 +787,611 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-memory operand form.  Same schedule, exchange and snapshots as
+// k_gibbs_pair, with the roles of the MMA operands swapped: the one-hot
+// states are the A operand (M = 128 chains, one TMEM lane per chain), written
+// by the generators into tensor memory with tcgen05.st, and the coupling
+// tile is the B operand (N = the block's rows (i,a) rounded up to 16, K-major
+// 128B-swizzled in shared memory as loaded by TMA).  The accumulator then
+// holds one chain per TMEM lane and one row (i,a) per column, so each drawer
+// thread reads its own chain's fields of a site straight from TMEM.  Per
+// 64-column K chunk the shared-memory traffic is the 32 KB coupling tile
+// written by TMA and read once by the MMAs; the one-hot operand never touches
+// shared memory.
+//
+// TMEM (512 columns): accumulators of own blocks j = kb/2 in columns
+// [128 (j%2), +128); one-hot ring slot s in columns [256 + 32 s, +32), two
+// fp16 K elements per column (the lower half holds the even element).
+// Warps: 0 TMA producer; 1 TMEM allocation and the MMA thread; 2-5 drawers
+// (chain 32 (warp%4) + lane, the TMEM lane quarter a warp may access); 6-9
+// generators (same chain mapping).
+// ---------------------------------------------------------------------------
+constexpr int kTmNC = 128;  // chains per cluster = MMA M
+constexpr int kTmNAmax = 4;
+constexpr int kTmNB = 4;
+constexpr int kTmDraw = 128, kTmGen = 128;
+constexpr int kTmThreads = 64 + kTmDraw + kTmGen;
+constexpr uint32_t kTmCols = 512, kTmAccCols = 128, kTmOneHotCol = 256;
+constexpr int kTmNBars = 2 * kTmNAmax + 2 * kTmNB + 2 + 2 + 2 + 1 + 1 + 1;
+constexpr int kTmUrS = kBmax + 1;  // row stride (words) of the per-chain uniform table
+
+__host__ __device__ inline Smem smem_layout_tm(int na, int Lp, int B, int nK, int q)
+{
+    Smem s;
+    s.a = 0;
+    s.b = s.a + na * kSlotA;  // no shared-memory one-hot ring or field rows
+    s.st = s.b;
+    s.snap = s.st + kTmNC * st_stride(Lp);
+    s.corr = (s.snap + 4 * kTmNC * snap_stride(B) + 15) & ~15u;
+    s.hrow = s.corr + (uint32_t)corr_slots(B) * q * q4_of(q) * 4;  // [2][128]: h rows of own blocks j % 2
+    s.hs = s.hrow + 2 * kRowsA * 4;                                  // uniforms: [chain][kTmUrS]
+    s.jtab = s.hs + kTmNC * kTmUrS * 4;
+    s.bars = (s.jtab + nK * 4 + 15) & ~15u;
+    s.misc = s.bars + kTmNBars * 8;
+    s.total = s.misc + 16;
+    return s;
+}
+
+__device__ __forceinline__ void mma_f16_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr)
+{
+    uint32_t v;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
+    return v;
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+        "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+        "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+// The 32 registers (fp16 pairs, even element in the lower half) of a 64-element
+// one-hot row from bit masks of its +1 (0x3c00) and -1 (0xbc00) entries.  Per
+// 4-element nibble x: x * 0x00204081 = x + (x << 7) + (x << 14) + (x << 21)
+// holds four disjoint copies of x, in which bit b of copy b sits at bit 8b;
+// & 0x01010101 keeps those, so byte b is bit b of x.  The bytes are scaled to
+// the fp16 high bytes 0x3c / 0xbc and moved into place by byte permutes.
+template <bool MINUS>
+__device__ __forceinline__ void onehot_regs(uint64_t plus, uint64_t minus, uint32_t (&v)[32])
+{
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+        const uint32_t xp = (uint32_t)(plus >> (4 * n)) & 0xfu;
+        uint32_t w = ((xp * 0x00204081u) & 0x01010101u) * 0x3cu;
+        if (MINUS) {
+            const uint32_t xm = (uint32_t)(minus >> (4 * n)) & 0xfu;
+            w += ((xm * 0x00204081u) & 0x01010101u) * 0xbcu;
+        }
+        v[2 * n] = __byte_perm(w, 0u, 0x1404);      // bytes: 0, w0, 0, w1
+        v[2 * n + 1] = __byte_perm(w, 0u, 0x3424);  // bytes: 0, w2, 0, w3
+    }
+}
+
+// 1 << n, and 0 when n (as an unsigned amount) is 32 or more: PTX clamps
+// the shift amount, so out-of-range positions need no test.
+__device__ __forceinline__ uint32_t bit_at(int n)
+{
+    uint32_t r;
+    asm("shl.b32 %0, 1, %1;" : "=r"(r) : "r"(n));
+    return r;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Categorical draw from beta*log2(e)-scaled fields H[0..q) (entries q..QC
+// are -inf): weights 2^(H_a - max), prefix sums W_a, and the symbol is the
+// number of prefix sums <= u * W_{q-1}, capped at q-1; since the prefix sums
+// do not decrease this is the first a with u * W_{q-1} < W_a.
+template <int QC>
+__device__ __forceinline__ int draw_symbol(float (&H)[QC], int q, uint32_t r24)
+{
+    static_assert(QC % 8 == 0 && QC <= 32, "QC: q rounded up to a multiple of 8");
+    float m[8];  // maximum as a tree: QC -> 8 -> 4 -> 2 -> 1
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        m[a] = H[a];
+#pragma unroll
+        for (int k = 1; k < QC / 8; ++k) m[a] = fmaxf(m[a], H[a + 8 * k]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) m[a] = fmaxf(m[a], m[a + 4]);
+    const float mx = fmaxf(fmaxf(m[0], m[2]), fmaxf(m[1], m[3]));
+    float S = 0.0f;
+#pragma unroll
+    for (int a = 0; a < QC; ++a) {
+        S += ex2_approx(H[a] - mx);
+        H[a] = S;
+    }
+    const float thr = ((float)r24 * 5.9604644775390625e-8f) * S;
+    int n = 0;
+#pragma unroll
+    for (int a = 0; a < QC; ++a) n += H[a] <= thr ? 1 : 0;
+    return min(n, q - 1);
+}
+
+template <bool BATCH, int QC>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTmThreads, 1)
+    k_gibbs_pair_tm(const __grid_constant__ CUtensorMap tm_one, const __grid_constant__ PairArgs p_one,
+                    const PairItem *__restrict__ items)
+{
+    const PairItem *const item = BATCH ? items + (blockIdx.x >> 1) : nullptr;
+    const PairArgs &p = BATCH ? item->a : p_one;
+    const CUtensorMap *const tm_jp = BATCH ? &item->tm : &tm_one;
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    const int na = p.na;
+    const Smem lay = smem_layout_tm(na, p.Lp, p.B, p.nK, p.q);
+    uint8_t *st = base + lay.st;
+    uint8_t *snap = base + lay.snap;
+    const float4 *corr4 = reinterpret_cast<const float4 *>(base + lay.corr);
+    float *hrow = reinterpret_cast<float *>(base + lay.hrow);
+    unsigned short *jtab = reinterpret_cast<unsigned short *>(base + lay.jtab);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + lay.bars);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + lay.misc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(base + lay.misc + 4);
+    const uint32_t full_a = su32(bars), empty_a = full_a + 8 * kTmNAmax;
+    const uint32_t full_b = empty_a + 8 * kTmNAmax, empty_b = full_b + 8 * kTmNB;
+    const uint32_t acc_full = empty_b + 8 * kTmNB;  // [2], own block j = kb/2 in slot j % 2
+    const uint32_t acc_empty = acc_full + 16;       // [2]
+    const uint32_t ready = acc_empty + 16;          // [2], states after block kb: barrier kb % 2
+    const uint32_t snapready = ready + 16;          // CTA 0: next pair's snapshots taken
+    const uint32_t corr_bar = snapready + 8;        // staged coupling blocks of the own block
+    const uint32_t gen_done = corr_bar + 8;         // CTA 0: CTA 1's generators finished pair P's main chunks
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = (int)cluster_rank(), peer = r ^ 1;
+    const int q = p.q, L = p.L, Lp = p.Lp;
+    constexpr int NC = kTmNC;
+    const int Sst = st_stride(Lp), Ssn = snap_stride(p.B);
+    const size_t cta0 = BATCH ? (size_t)item->first : (size_t)(blockIdx.x >> 1) * NC;
+    const long long nblocks = p.nblocks;
+    const long long npairs = (nblocks + 1) / 2;
+    auto snap_of = [&](long long kb) { return snap + (size_t)((((kb >> 1) & 1) * 2 + (kb & 1)) * NC) * Ssn; };
+
+    if (tid == 0) {
+        for (int s = 0; s < kTmNAmax; ++s) {
+            mbar_init(full_a + 8 * s, 1);
+            mbar_init(empty_a + 8 * s, 1);
+        }
+        for (int s = 0; s < kTmNB; ++s) {
+            mbar_init(full_b + 8 * s, kTmGen / 32);
+            mbar_init(empty_b + 8 * s, 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(acc_full + 8 * s, 1);
+            mbar_init(acc_empty + 8 * s, kTmDraw / 32);
+            mbar_init(ready + 8 * s, kTmDraw);
+        }
+        mbar_init(snapready, kTmDraw);
+        mbar_init(corr_bar, 1);
+        mbar_init(gen_done, kTmGen / 32);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(kTmCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int k = tid; k < NC * Lp; k += kTmThreads) {
+        const int c = k / Lp, x = k - c * Lp;
+        const size_t m = cta0 + c;
+        st[c * Sst + x] = (m < (size_t)p.M && x < L) ? p.states[m * L + x] : 0;
+    }
+    for (int c = tid; c < p.nK; c += kTmThreads) {
+        const int k0 = c * kKC;
+        jtab[2 * c] = (unsigned short)min(L - 1, k0 / q);
+        jtab[2 * c + 1] = (unsigned short)min(L - 1, (k0 + kKC - 1) / q);
+    }
+    __syncthreads();
+    for (long long kb = 0; kb < 2 && kb < nblocks; ++kb) {  // snapshots of pair 0
+        const Blk g = blk_of(p, kb);
+        uint8_t *sn = snap_of(kb);
+        for (int k = tid; k < NC * g.Bk; k += kTmThreads) {
+            const int c = k / g.Bk, x = k - c * g.Bk;
+            sn[c * Ssn + x] = st[c * Sst + g.i0 + x];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    cluster_sync_all();  // both CTAs' barriers are initialised before any remote arrival
+    const uint32_t tmem = *tmem_slot;
+
+    auto stage_corr = [&](long long kb) {
+        const Blk g = blk_of(p, kb);
+        const uint32_t row = (uint32_t)q * (uint32_t)q4_of(q);
+        const uint32_t bytes = (uint32_t)corr_slots(g.Bk) * row * 4u;
+        mbar_expect_tx(corr_bar, bytes);
+        if (bytes > 0)
+            bulk_g2s(su32(base + lay.corr), p.Jc + (size_t)(kb % p.nb) * corr_slots(p.B) * row, bytes, corr_bar);
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            long long issued = 0;
+            int sa = 0, lap = 0;
+            bool ok = true;
+            for (long long P = 0; P <= npairs && ok; ++P)
+                for (int step = 0; step < 4 && ok; ++step) {
+                    const Seg sg = seg_info(p, P, step, r);
+                    const int r0 = sg.n > 0 ? (int)(sg.t % p.nb) * kRowsA : 0;
+                    for (int k = 0; k < sg.n && ok; ++k) {
+                        const int c = seg_chunk(sg, k);
+                        if (lap > 0 && !mbar_wait(empty_a + 8 * sa, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t dst = su32(base + lay.a + sa * kSlotA), bar = full_a + 8 * sa;
+                        mbar_expect_tx(bar, (uint32_t)kSlotA);
+                        tma_load_3d(dst, tm_jp, 0, r0, 2 * c, bar);  // hi slab then lo slab of 128 rows
+                        ++issued;
+                        if (++sa == na) {
+                            sa = 0;
+                            ++lap;
+                        }
+                    }
+                }
+            if (*abort_flag) {
+                volatile int no_abort = 0;
+                for (long long u = issued > na ? issued - na : 0; u < issued; ++u)
+                    mbar_wait(full_a + 8 * (int)(u % na), (uint32_t)((u / na) & 1), &no_abort, p.err);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            // kind::f16: D F32 (bit 4), A = B = F16, both K-major, N >> 3 at 17, M >> 4 at 24;
+            // A (one-hot, M = 128 chains) from TMEM, B (coupling rows, N = nmma) from shared memory.
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(p.nmma >> 3) << 17) | ((uint32_t)(kTmNC >> 4) << 24);
+            int sa = 0, sb = 0;
+            uint32_t pha = 0, phb = 0;
+            bool ok = true;
+            for (long long P = 0; P <= npairs && ok; ++P)
+                for (int step = 0; step < 4 && ok; ++step) {
+                    const Seg sg = seg_info(p, P, step, r);
+                    const long long j = sg.t >> 1;  // own block index
+                    for (int k = 0; k < sg.n && ok; ++k) {
+                        const int c = seg_chunk(sg, k);
+                        const bool first = !sg.delta && c == 0;
+                        if (!mbar_wait(full_b + 8 * sb, phb, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        if (!mbar_wait(full_a + 8 * sa, pha, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        if (first && j >= 2 &&
+                            !mbar_wait(acc_empty + 8 * (int)(j & 1), (uint32_t)(((j - 2) >> 1) & 1), abort_flag,
+                                       p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t at = tmem + kTmOneHotCol + (uint32_t)sb * 32u;
+                        const uint32_t bh = su32(base + lay.a + sa * kSlotA);
+                        const uint64_t dh = desc_sw128(bh), dl = desc_sw128(bh + kTileA);
+                        const uint32_t dcol = tmem + (uint32_t)(j & 1) * kTmAccCols;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {  // +32 bytes along K = +2 in the start field
+                            mma_f16_ts(dcol, at + kk * 8, dh + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
+                            mma_f16_ts(dcol, at + kk * 8, dl + 2 * kk, idesc, 1u);
+                        }
+                        mma_commit(empty_a + 8 * sa);
+                        if (++sa == na) {
+                            sa = 0;
+                            pha ^= 1u;
+                        }
+                        mma_commit(empty_b + 8 * sb);
+                        if (++sb == kTmNB) {
+                            sb = 0;
+                            phb ^= 1u;
+                        }
+                    }
+                    if (ok && sg.commit_kb >= 0) mma_commit(acc_full + 8 * (int)((sg.commit_kb >> 1) & 1));
+                }
+        }
+    } else if (warp < 6) {
+        // ------------------------------------------------------------ drawers (warps 2-5)
+        // Uniform control flow: every drawer runs the whole loop nest and meets
+        // every named barrier; after an abort the work is skipped.
+        const int w = tid - 64;                  // 0..127
+        const int lane_base = 32 * (warp & 3);   // TMEM lane quarter of this warp
+        const int ch = lane_base + lane;         // chain (TMEM lane) of this thread
+        const int qv = q4_of(q) >> 2;            // float4s per padded coupling row
+        const uint32_t st_peer = peer_addr(su32(st), (uint32_t)peer);
+        const uint32_t ready_peer = peer_addr(ready, (uint32_t)peer);
+        const uint64_t m = p.chain0 + cta0 + ch;
+        uint32_t *const urow = reinterpret_cast<uint32_t *>(base + lay.hs) + ch * kTmUrS;
+        // Ahead of own block kb (neither depends on the states): the Philox
+        // numerators of its sites into this chain's row of the uniform table
+        // (two independent streams at a time), and its h rows into buffer j % 2.
+        auto prefetch = [&](long long kb) {
+            const Blk g = blk_of(p, kb);
+            const uint64_t sweep = p.sweep0 + (uint64_t)(kb / p.nb);
+            for (int pp = 0; pp < g.Bk; pp += 2) {
+                const uint32_t u0 = bm_u24(p.seed, m, sweep, (uint64_t)(g.i0 + pp), 0);
+                const uint32_t u1 = bm_u24(p.seed, m, sweep, (uint64_t)(g.i0 + pp + 1), 0);
+                urow[pp] = u0;
+                if (pp + 1 < g.Bk) urow[pp + 1] = u1;
+            }
+            float *hr = hrow + ((kb >> 1) & 1) * kRowsA;
+            for (int k = w; k < g.Bk * q; k += kTmDraw) hr[k] = p.h[(size_t)g.i0 * q + k];
+        };
+        bool ok = true;
+        long long staged = 0;
+        if (w == 0 && r < nblocks) {
+            stage_corr(r);
+            staged = 1;
+        }
+        if (r < nblocks) prefetch(r);
+        for (long long kb = r; kb < nblocks; kb += 2) {
+            const long long j = kb >> 1;
+            const Blk g = blk_of(p, kb);
+            const int slot = (int)(j & 1);
+            const float *hr = hrow + slot * kRowsA;
+            if (ok && !mbar_wait(acc_full + 8 * slot, (uint32_t)((j >> 1) & 1), abort_flag, p.err)) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (ok && !mbar_wait(corr_bar, (uint32_t)(j & 1), abort_flag, p.err)) ok = false;
+            ok = !named_bar_or(1, kTmDraw, !ok || *abort_flag);
+            const uint8_t *old = snap_of(kb) + ch * Ssn;
+            const uint32_t tacc = tmem + ((uint32_t)lane_base << 16) + (uint32_t)slot * kTmAccCols;
+            // the fields of site pp+1 are loaded from TMEM while site pp is drawn
+            // QC columns from the site's first (the ones past q belong to the
+            // next site or lie past the block: masked below)
+            uint32_t v[QC];
+            if (ok) {
+#pragma unroll
+                for (int a = 0; a < QC; ++a) v[a] = tmem_ld1(tacc + (uint32_t)a);
+            }
+            for (int pp = 0; pp < g.Bk && ok; ++pp) {
+                const int i = g.i0 + pp;
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float H[QC];
+#pragma unroll
+                for (int a = 0; a < QC; ++a) {
+                    asm volatile("" : "+r"(v[a]));  // not before the wait
+                    H[a] = hr[pp * q + a] + __uint_as_float(v[a]);
+                }
+                if (pp + 1 < g.Bk) {
+#pragma unroll
+                    for (int a = 0; a < QC; ++a) v[a] = tmem_ld1(tacc + (uint32_t)((pp + 1) * q + a));
+                }
+                const uint32_t r24 = urow[pp];
+                // sites jj < pp of the block redrawn since the MMAs: + J_ij(., new) - J_ij(., old)
+                const float4 *cb = corr4 + (size_t)(pp * (pp - 1) / 2) * q * qv;
+                for (int jj = 0; jj < pp; ++jj) {
+                    const int sn = st[ch * Sst + g.i0 + jj], so = old[jj];
+                    if (sn == so) continue;
+                    const float4 *rn = cb + (jj * q + sn) * qv, *ro = cb + (jj * q + so) * qv;
+#pragma unroll
+                    for (int a4 = 0; a4 < QC / 4; ++a4) {  // past q4: the next row or the h rows, masked
+                        const float4 vn = rn[a4], vo = ro[a4];
+                        H[4 * a4] += vn.x - vo.x;
+                        H[4 * a4 + 1] += vn.y - vo.y;
+                        H[4 * a4 + 2] += vn.z - vo.z;
+                        H[4 * a4 + 3] += vn.w - vo.w;
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < QC; ++a) H[a] = a < q ? H[a] * p.beta_l2e : -INFINITY;
+                st[ch * Sst + i] = (uint8_t)draw_symbol<QC>(H, q, r24);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + 8 * slot);
+            named_bar_sync(1, kTmDraw);  // the staged coupling blocks are free again
+            if (w == 0 && ok && !*abort_flag && kb + 2 < nblocks) {
+                stage_corr(kb + 2);
+                ++staged;
+            }
+            // CTA 1: the next pair's snapshots, before block kb is published
+            // (CTA 0 starts rewriting block kb+1's sites once it has it).
+            if (r == 1 && kb + 1 < nblocks) {
+                if (ok && !mbar_wait_cl(ready + 8 * (int)((kb - 1) & 1), (uint32_t)(((kb - 1) >> 1) & 1), abort_flag,
+                                        p.err))
+                    ok = false;
+                if (ok)
+                    for (long long nb2 = kb + 1; nb2 <= kb + 2 && nb2 < nblocks; ++nb2) {
+                        const Blk gn = blk_of(p, nb2);
+                        uint8_t *sn = snap_of(nb2) + ch * Ssn;
+                        for (int x = 0; x < gn.Bk; ++x) sn[x] = st[ch * Sst + gn.i0 + x];
+                    }
+            }
+            // Copy block kb's new states into the peer's copy.  CTA 0 first waits
+            // until CTA 1's generators have finished pair j's main chunks, which
+            // still read block kb's pre-redraw states from CTA 1's copy.
+            if (r == 0 && ok && !mbar_wait_cl(gen_done, (uint32_t)(j & 1), abort_flag, p.err)) ok = false;
+            if (ok)
+                for (int x = 0; x < g.Bk; ++x)
+                    st_cluster_u8(st_peer + (uint32_t)(ch * Sst + g.i0 + x), (unsigned short)st[ch * Sst + g.i0 + x]);
+            // publish block kb: own generator and the peer
+            mbar_arrive(ready + 8 * (int)(kb & 1));
+            mbar_arrive_peer(ready_peer + 8 * (uint32_t)(kb & 1));
+            if (ok && kb + 2 < nblocks) prefetch(kb + 2);
+            // CTA 0: the next pair's snapshots once block kb+1 has arrived
+            if (r == 0 && kb + 1 < nblocks) {
+                if (ok && !mbar_wait_cl(ready + 8 * (int)((kb + 1) & 1), (uint32_t)(((kb + 1) >> 1) & 1), abort_flag,
+                                        p.err))
+                    ok = false;
+                if (ok)
+                    for (long long nb2 = kb + 2; nb2 <= kb + 3 && nb2 < nblocks; ++nb2) {
+                        const Blk gn = blk_of(p, nb2);
+                        uint8_t *sn = snap_of(nb2) + ch * Ssn;
+                        for (int x = 0; x < gn.Bk; ++x) sn[x] = st[ch * Sst + gn.i0 + x];
+                    }
+                mbar_arrive(snapready);
+            }
+        }
+        if (!ok) *abort_flag = 1;
+        if (w == 0 && *abort_flag && staged > 0) {
+            volatile int no_abort = 0;
+            mbar_wait(corr_bar, (uint32_t)((staged - 1) & 1), &no_abort, p.err);
+        }
+    } else {
+        // ------------------------------------------------------------ generators (warps 6-9)
+        const int lane_base = 32 * (warp & 3);
+        const int ch = lane_base + lane;  // operand row (TMEM lane) of chain ch
+        const int st_o = (int)lay.st + ch * Sst;  // byte offsets from base: this chain's state row
+        const int wrow = ch * Ssn;
+        const uint32_t tone = tmem + ((uint32_t)lane_base << 16) + kTmOneHotCol;
+        const uint32_t gen_done_peer = peer_addr(gen_done, (uint32_t)peer);
+        int sb = 0, lap = 0;
+        int pend = -1;  // ring slot whose one-hot store is still in flight
+        // The previous chunk's store has completed: hand its slot to the MMA.
+        auto flush = [&]() {
+            if (pend >= 0) {
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full_b + 8 * pend);
+                pend = -1;
+            }
+        };
+        bool ok = true;
+        for (long long P = 0; P <= npairs && ok; ++P) {
+            int s0lo = L, s0n = 0, s1lo = L, s1n = 0;  // blocks 2P-2, 2P-1: first site and size
+            int ps0 = (int)lay.snap, ps1 = ps0;         // and their snapshot rows (offsets from base)
+            if (P >= 1) {
+                const Blk g0 = blk_of(p, 2 * P - 2), g1 = blk_of(p, 2 * P - 1);
+                s0lo = g0.i0;
+                s0n = g0.Bk;
+                s1lo = g1.i0;
+                s1n = g1.Bk;
+                ps0 = (int)(snap_of(2 * P - 2) - base) + wrow;
+                ps1 = (int)(snap_of(2 * P - 1) - base) + wrow;
+            }
+            // state of site jj as the main chunks see it (blocks being redrawn: snapshot)
+            auto state = [&](int jj) {
+                int o = st_o + jj;
+                o = (unsigned)(jj - s0lo) < (unsigned)s0n ? ps0 + (jj - s0lo) : o;
+                o = (unsigned)(jj - s1lo) < (unsigned)s1n ? ps1 + (jj - s1lo) : o;
+                return (int)base[o];
+            };
+            for (int step = 0; step < 4 && ok; ++step) {
+                const Seg sg = seg_info(p, P, step, r);
+                if (sg.n > 0 && sg.wait_kind != 0) {
+                    flush();  // the awaited block may need that chunk's MMAs
+                    const uint32_t bar = sg.wait_kind == 1 ? ready + 8 * (uint32_t)(sg.wait_kb & 1) : snapready;
+                    if (!mbar_wait_cl(bar, (uint32_t)((sg.wait_kb >> 1) & 1), abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                for (int k = 0; k < sg.n; ++k) {
+                    const int c = seg_chunk(sg, k);
+                    const int k0 = c * kKC;
+                    // bit e of (plus, minus): element k0 + e of the row is +1 / -1
+                    uint32_t pl0 = 0, pl1 = 0, mi0 = 0, mi1 = 0;
+                    if (!sg.delta) {
+                        const int jlo = jtab[2 * c], jhi = jtab[2 * c + 1];
+                        if (jhi - jlo < 8) {  // q >= 8: independent loads, no branch (sites past jhi: no bit)
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                const int jj = min(jlo + t, jhi);
+                                const int pos = jlo + t <= jhi ? jj * q + state(jj) - k0 : -1;
+                                pl0 |= bit_at(pos);
+                                pl1 |= bit_at(pos - 32);
+                            }
+                        } else {
+                            for (int jj = jlo; jj <= jhi; ++jj) {
+                                const int pos = jj * q + state(jj) - k0;
+                                pl0 |= bit_at(pos);
+                                pl1 |= bit_at(pos - 32);
+                            }
+                        }
+                    } else {
+                        for (int u = 0; u < 2; ++u) {
+                            const long long db = u == 0 ? sg.d0 : sg.d1;
+                            if (db < 0) continue;
+                            const Blk gd = blk_of(p, db);
+                            const int po = u == 0 ? ps0 : ps1;  // d0 = 2P-2, d1 = 2P-1
+                            for (int x = 0; x < gd.Bk; ++x) {
+                                const int jj = gd.i0 + x;
+                                const int sn = base[st_o + jj], so = base[po + x];
+                                if (sn == so) continue;
+                                const int pn = jj * q + sn - k0, pd = jj * q + so - k0;
+                                pl0 |= bit_at(pn);
+                                pl1 |= bit_at(pn - 32);
+                                mi0 |= bit_at(pd);
+                                mi1 |= bit_at(pd - 32);
+                            }
+                        }
+                    }
+                    const uint64_t pl = ((uint64_t)pl1 << 32) | pl0, mi = ((uint64_t)mi1 << 32) | mi0;
+                    if (lap > 0 && !mbar_wait(empty_b + 8 * sb, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    uint32_t v[32];
+                    if (sg.delta)
+                        onehot_regs<true>(pl, mi, v);
+                    else
+                        onehot_regs<false>(pl, 0ull, v);
+                    flush();
+                    tmem_st32(tone + (uint32_t)sb * 32u, v);  // completes while the next chunk is built
+                    pend = sb;
+                    if (++sb == kTmNB) {
+                        sb = 0;
+                        ++lap;
+                    }
+                }
+                // CTA 1: pair P's main chunks are read; CTA 0 may now overwrite
+                // block 2P's sites in this CTA's copy of the states
+                if (ok && r == 1 && step == 2 && 2 * P < nblocks) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_peer(gen_done_peer);
+                }
+            }
+        }
+        flush();
+        if (!ok) *abort_flag = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmCols) : "memory");
+    // No remote store or arrival into either CTA is in flight past this
+    // barrier; then each CTA reads the other's abort flag, and the second
+    // barrier keeps both CTAs resident until those reads are done.
+    cluster_sync_all();
+    const bool bad = *abort_flag != 0 || ld_cluster_u32(peer_addr(su32((const void *)abort_flag), (uint32_t)peer)) != 0;
+    cluster_sync_all();
+    if (bad) return;
+    const int half = NC / 2;  // CTA r writes back chains 2c + r
+    for (int k = tid; k < half * L; k += kTmThreads) {
+        const int cc = k / L, x = k - cc * L;
+        const int c = 2 * cc + r;
+        const size_t mm = cta0 + c;
+        if (mm < (size_t)p.M) p.states[mm * L + x] = st[c * Sst + x];
+    }
+}
+
 // Jc[blk][slot][b][a4] = J_ij(a, b) for i = blk*B + pi, j = blk*B + pj,
 // slot = pi*(pi-1)/2 + pj (pi > pj); zero for a >= q or i >= L.
 __global__ void k_build_corr(const float *__restrict__ J, float *__restrict__ Jc, int L, int q, int B, int nb)
@@ -875,6 +1495,69 @@ void fill_args(const bm_model_s *m, const bm_chains_s *c, int NC, int nsweeps, f
     a.X = a.nK / 2;
     a.acc_stride = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;
     a.tmem_cols = 2 * a.acc_stride;
+    a.na = 0;
+    a.nmma = 0;
+}
+
+// The tensor-memory operand kernel for q rounded up to 8.
+template <bool BATCH>
+int launch_tm(int q, int grid, size_t smem, cudaStream_t st, const CUtensorMap &tm, const PairArgs &a,
+              const PairItem *items)
+{
+    auto go = [&](auto kern) -> int {
+        BM_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, kTmThreads, smem, st>>>(tm, a, items);
+        BM_CK_LAUNCH("k_gibbs_pair_tm");
+        return BM_OK;
+    };
+    switch ((q + 7) / 8) {
+    case 1: return go(k_gibbs_pair_tm<BATCH, 8>);
+    case 2: return go(k_gibbs_pair_tm<BATCH, 16>);
+    case 3: return go(k_gibbs_pair_tm<BATCH, 24>);
+    default: return go(k_gibbs_pair_tm<BATCH, 32>);
+    }
+}
+
+// Coupling ring slots of the tensor-memory operand form for this shape (as
+// many as fit one CTA's shared memory, 4 down to 2), 0 when it does not fit.
+int tm_ring(const bm_model_s *m)
+{
+    if (m->L < 2 || m->L > 65535 || m->q > kQmax) return 0;
+    const int B = bm_split_block_sites(m->L, m->q);
+    if (B > kBmax || B * m->q > kRowsA) return 0;
+    const int Lp = (m->L + 15) & ~15, nK = (m->L * m->q + kKC - 1) / kKC;
+    for (int na = kTmNAmax; na >= 2; --na)
+        if (smem_layout_tm(na, Lp, B, nK, m->q).total + 1024 <= 227 * 1024) return na;
+    return 0;
+}
+
+// Ring slots when the sweep takes the tensor-memory operand form, else 0.
+// That form wins where a block's draws outweigh its K chunks (measured at
+// L=120 q=5 and L=64 q=21: 1.5-1.9x); where the chunks dominate (q=21,
+// L >= 120) the one-hot generators set its pace and the shared-memory
+// operand form is faster.
+int tm_form(const bm_model_s *m)
+{
+    const int na = tm_ring(m);
+    if (na == 0) return 0;
+    const int nK = (m->L * m->q + kKC - 1) / kKC;
+    return nK <= 4 * bm_split_block_sites(m->L, m->q) ? na : 0;
+}
+
+size_t smem_bytes_tm(const bm_model_s *m, int na)
+{
+    const int B = bm_split_block_sites(m->L, m->q);
+    return (size_t)smem_layout_tm(na, (m->L + 15) & ~15, B, (m->L * m->q + kKC - 1) / kKC, m->q).total + 1024;
+}
+
+void fill_args_tm(const bm_model_s *m, const bm_chains_s *c, int na, int nsweeps, float beta, uint8_t *states,
+                  PairArgs &a)
+{
+    fill_args(m, c, kTmNC, nsweeps, beta, states, a);
+    a.na = na;
+    a.nmma = (a.B * a.q + 15) & ~15;
+    a.tmem_cols = kTmCols;
+    a.acc_stride = kTmAccCols;
 }
 
 // The tensor-core layouts (split J, in-block corrections) of the live J.
@@ -896,10 +1579,14 @@ int bm_corr_prepare(bm_model_s *m, cudaStream_t st)
 // <= 160), or 0 when the shape does not fit one CTA's shared memory or L < 2.
 int bm_gibbs_pair_chains_per_cluster(const bm_model_s *m, int M)
 {
+    if (tm_form(m) > 0) return kTmNC;
     const int ncl = max_clusters(m);
     const int want = std::max(16, (((M + ncl - 1) / ncl) + 15) & ~15);
     return fit_nc(m, want);
 }
+
+// True when the two-CTA sweep takes its tensor-memory operand form.
+bool bm_gibbs_pair_tm(const bm_model_s *m) { return tm_form(m) > 0; }
 
 // Waves of clusters the two-CTA sweep of M chains needs (0: does not fit).
 int bm_gibbs_pair_waves(const bm_model_s *m, int M)
@@ -917,6 +1604,15 @@ int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta,
     {
         const int rc = model_prepare(m, st);
         if (rc != BM_OK) return rc;
+    }
+    const int na = tm_form(m);
+    if (na > 0) {
+        PairArgs a;
+        fill_args_tm(m, c, na, nsweeps, beta, c->s, a);
+        const size_t smem = smem_bytes_tm(m, na);
+        const int nclusters = (c->M + kTmNC - 1) / kTmNC;
+        return launch_tm<false>(a.q, 2 * nclusters, smem, st, *reinterpret_cast<const CUtensorMap *>(m->tmap_jp), a,
+                                nullptr);
     }
     PairArgs a;
     fill_args(m, c, NC, nsweeps, beta, c->s, a);

@@ -32,12 +32,30 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+// Like mbar_try, but a thread whose phase is not complete is suspended until
+// it completes or kSuspendNs pass (the hint bounds the suspension), so that a
+// waiting warp takes no issue slots from the warps doing the work.
+constexpr uint32_t kSuspendNs = 20000;
+
+__device__ __forceinline__ bool mbar_try_suspend(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
 {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     for (;;) {
-        if (mbar_try(bar, parity)) return true;
+        if (mbar_try_suspend(bar, parity)) return true;
         if (*abort_flag) return false;
         if (gtimer() - t0 > kWaitNs) {
             *abort_flag = 1;

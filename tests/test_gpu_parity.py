@@ -623,14 +623,17 @@ def test_sweep_engine_resolution(bm):
     # small problems go to the gather; large small-alphabet ones to the tensor cores
     h48, J48 = synth.planted_local_model(48, 21, 3)
     assert bm.bm_model_sweep_engine(load(bm, h48, J48), 1000) == bm.BM_ENGINE_SIMT
+    # alphabets of 4-8 symbols with many sites per block: the two-CTA sweep
+    # (tensor-memory operand form) from L = 120 and M = 4096
     h4, J4 = synth.planted_local_model(256, 4, 3)
     m4 = load(bm, h4, J4)
-    assert bm.bm_model_sweep_engine(m4, 5000) == bm.BM_ENGINE_MMA
+    assert bm.bm_model_sweep_engine(m4, 5000) == bm.BM_ENGINE_MMA_PAIR
     assert bm.bm_model_sweep_engine(m4, 500) == bm.BM_ENGINE_SIMT
     h6, J6 = synth.planted_local_model(256, 5, 3)
     m6 = load(bm, h6, J6)
-    assert bm.bm_model_sweep_engine(m6, 20000) == bm.BM_ENGINE_MMA
-    assert bm.bm_model_sweep_engine(m6, 5000) == bm.BM_ENGINE_SIMT
+    assert bm.bm_model_sweep_engine(m6, 20000) == bm.BM_ENGINE_MMA_PAIR
+    assert bm.bm_model_sweep_engine(m6, 5000) == bm.BM_ENGINE_MMA_PAIR
+    assert bm.bm_model_sweep_engine(m6, 2000) == bm.BM_ENGINE_SIMT
     with pytest.raises(bm.BmError) as e:
         bm.bm_model_sweep_engine(m5, 0)
     assert e.value.code == bm.BM_EINVAL
