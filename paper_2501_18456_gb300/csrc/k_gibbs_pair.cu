@@ -58,7 +58,7 @@
 // cluster barrier before leaving, and the chains are written back only when
 // neither CTA aborted.
 //
-// Batch mode (k_gibbs_pair<true>): cluster k runs work item k of a list,
+// Batch mode (k_gibbs_pair<true, QC>): cluster k runs work item k of a list,
 // i.e. its own model's arguments, TMA descriptor and chain tile, so many
 // models of uneven length are swept in one launch.
 #include "bm_internal.cuh"
@@ -310,9 +310,47 @@ __device__ Seg seg_info(const PairArgs &p, long long P, int step, int r)
     return s;
 }
 
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Categorical draw from beta*log2(e)-scaled fields H[0..q) (entries q..QC
+// are -inf): weights 2^(H_a - max), prefix sums W_a, and the symbol is the
+// number of prefix sums <= u * W_{q-1}, capped at q-1; since the prefix sums
+// do not decrease this is the first a with u * W_{q-1} < W_a.
+template <int QC>
+__device__ __forceinline__ int draw_symbol(float (&H)[QC], int q, uint32_t r24)
+{
+    static_assert(QC % 8 == 0 && QC <= 32, "QC: q rounded up to a multiple of 8");
+    float m[8];  // maximum as a tree: QC -> 8 -> 4 -> 2 -> 1
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        m[a] = H[a];
+#pragma unroll
+        for (int k = 1; k < QC / 8; ++k) m[a] = fmaxf(m[a], H[a + 8 * k]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) m[a] = fmaxf(m[a], m[a + 4]);
+    const float mx = fmaxf(fmaxf(m[0], m[2]), fmaxf(m[1], m[3]));
+    float S = 0.0f;
+#pragma unroll
+    for (int a = 0; a < QC; ++a) {
+        S += ex2_approx(H[a] - mx);
+        H[a] = S;
+    }
+    const float thr = ((float)r24 * 5.9604644775390625e-8f) * S;
+    int n = 0;
+#pragma unroll
+    for (int a = 0; a < QC; ++a) n += H[a] <= thr ? 1 : 0;
+    return min(n, q - 1);
+}
+
 // BATCH: cluster k runs items[k] (its own model, tensor map and chain tile);
 // otherwise every cluster runs the launch arguments on chains k*NC ...
-template <bool BATCH>
+template <bool BATCH, int QC>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_gibbs_pair(const __grid_constant__ CUtensorMap tm_one, const __grid_constant__ PairArgs p_one,
                  const PairItem *__restrict__ items)
@@ -519,6 +557,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             const Blk g = blk_of(p, kb);
             const int slot = (int)(j & 1);
             const uint64_t sweep = p.sweep0 + (uint64_t)(kb / p.nb);
+            // the block's Philox numerators (independent of the states) while the
+            // accumulator fills, two independent streams at a time
+            uint32_t ur[kBmax];
+            if (w < NC) {
+                const uint64_t m = p.chain0 + cta0 + w;
+                for (int pp = 0; pp < g.Bk; pp += 2) {
+                    const uint32_t u0 = bm_u24(p.seed, m, sweep, (uint64_t)(g.i0 + pp), 0);
+                    const uint32_t u1 = bm_u24(p.seed, m, sweep, (uint64_t)(g.i0 + pp + 1), 0);
+                    ur[pp] = u0;
+                    if (pp + 1 < g.Bk) ur[pp + 1] = u1;
+                }
+            }
             if (ok && !mbar_wait(acc_full + 8 * slot, (uint32_t)((j >> 1) & 1), abort_flag, p.err)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int k = w; k < g.Bk * q; k += kDraw) hrow[k] = p.h[(size_t)g.i0 * q + k];
@@ -545,20 +595,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 const int i = g.i0 + pp;
                 if (w < NC) {
                     const int ch = w;
-                    const uint64_t m = p.chain0 + cta0 + ch;
-                    // the uniform first: it does not depend on the states
-                    const uint32_t r24 = bm_u24(p.seed, m, sweep, (uint64_t)i, 0);
-                    float H[32];
+                    const uint32_t r24 = ur[pp];
+                    // QC/4 float4s per row: past q the entries are masked below
+                    float H[QC];
                     const float4 *hs4 = reinterpret_cast<const float4 *>(Hs + ch * HS);
 #pragma unroll
-                    for (int a4 = 0; a4 < 8; ++a4)
-                        if (a4 < qv) {
-                            const float4 t = hs4[a4];
-                            H[4 * a4] = t.x;
-                            H[4 * a4 + 1] = t.y;
-                            H[4 * a4 + 2] = t.z;
-                            H[4 * a4 + 3] = t.w;
-                        }
+                    for (int a4 = 0; a4 < QC / 4; ++a4) {
+                        const float4 t = hs4[a4];
+                        H[4 * a4] = t.x;
+                        H[4 * a4 + 1] = t.y;
+                        H[4 * a4 + 2] = t.z;
+                        H[4 * a4 + 3] = t.w;
+                    }
                     // sites jj < pp of the block redrawn since the MMAs: + J_ij(., new) - J_ij(., old)
                     const float4 *cb = corr4 + (size_t)(pp * (pp - 1) / 2) * q * qv;
                     for (int jj = 0; jj < pp; ++jj) {
@@ -566,35 +614,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         if (sn == so) continue;
                         const float4 *rn = cb + (jj * q + sn) * qv, *ro = cb + (jj * q + so) * qv;
 #pragma unroll
-                        for (int a4 = 0; a4 < 8; ++a4)
-                            if (a4 < qv) {
-                                const float4 vn = rn[a4], vo = ro[a4];
-                                H[4 * a4] += vn.x - vo.x;
-                                H[4 * a4 + 1] += vn.y - vo.y;
-                                H[4 * a4 + 2] += vn.z - vo.z;
-                                H[4 * a4 + 3] += vn.w - vo.w;
-                            }
+                        for (int a4 = 0; a4 < QC / 4; ++a4) {  // past q4: the next row or the h rows, masked
+                            const float4 vn = rn[a4], vo = ro[a4];
+                            H[4 * a4] += vn.x - vo.x;
+                            H[4 * a4 + 1] += vn.y - vo.y;
+                            H[4 * a4 + 2] += vn.z - vo.z;
+                            H[4 * a4 + 3] += vn.w - vo.w;
+                        }
                     }
-                    float mx = -INFINITY;
 #pragma unroll
-                    for (int a = 0; a < 32; ++a)
-                        if (a < q) {
-                            H[a] *= p.beta_l2e;
-                            mx = fmaxf(mx, H[a]);
-                        }
-                    float S = 0.0f;
-#pragma unroll
-                    for (int a = 0; a < 32; ++a)
-                        if (a < q) {
-                            S += exp2f(H[a] - mx);
-                            H[a] = S;  // prefix sums of exp(beta H_a - max_b beta H_b)
-                        }
-                    const float thr = ((float)r24 * 5.9604644775390625e-8f) * S;
-                    int pick = q - 1;
-#pragma unroll
-                    for (int a = 31; a >= 0; --a)
-                        if (a < q && thr < H[a]) pick = a;
-                    st[ch * Sst + i] = (uint8_t)pick;
+                    for (int a = 0; a < QC; ++a) H[a] = a < q ? H[a] * p.beta_l2e : -INFINITY;
+                    st[ch * Sst + i] = (uint8_t)draw_symbol<QC>(H, q, r24);
                 }
                 named_bar_sync(1, kDraw);  // Hs is rewritten for the next site
             }
@@ -889,44 +919,6 @@ __device__ __forceinline__ uint32_t bit_at(int n)
     uint32_t r;
     asm("shl.b32 %0, 1, %1;" : "=r"(r) : "r"(n));
     return r;
-}
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Categorical draw from beta*log2(e)-scaled fields H[0..q) (entries q..QC
-// are -inf): weights 2^(H_a - max), prefix sums W_a, and the symbol is the
-// number of prefix sums <= u * W_{q-1}, capped at q-1; since the prefix sums
-// do not decrease this is the first a with u * W_{q-1} < W_a.
-template <int QC>
-__device__ __forceinline__ int draw_symbol(float (&H)[QC], int q, uint32_t r24)
-{
-    static_assert(QC % 8 == 0 && QC <= 32, "QC: q rounded up to a multiple of 8");
-    float m[8];  // maximum as a tree: QC -> 8 -> 4 -> 2 -> 1
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        m[a] = H[a];
-#pragma unroll
-        for (int k = 1; k < QC / 8; ++k) m[a] = fmaxf(m[a], H[a + 8 * k]);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) m[a] = fmaxf(m[a], m[a + 4]);
-    const float mx = fmaxf(fmaxf(m[0], m[2]), fmaxf(m[1], m[3]));
-    float S = 0.0f;
-#pragma unroll
-    for (int a = 0; a < QC; ++a) {
-        S += ex2_approx(H[a] - mx);
-        H[a] = S;
-    }
-    const float thr = ((float)r24 * 5.9604644775390625e-8f) * S;
-    int n = 0;
-#pragma unroll
-    for (int a = 0; a < QC; ++a) n += H[a] <= thr ? 1 : 0;
-    return min(n, q - 1);
 }
 
 template <bool BATCH, int QC>
@@ -1437,14 +1429,14 @@ int max_clusters(const bm_model_s *m)
     std::call_once(g_clusters_once[dev], [&] {
         int n = (m->num_sms > 0 ? m->num_sms : 2) / 2;
         const int smem = 200 * 1024;  // any size above half an SM's shared memory: one CTA per SM
-        if (cudaFuncSetAttribute(k_gibbs_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+        if (cudaFuncSetAttribute(k_gibbs_pair<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
             cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(2, 1, 1);
             cfg.blockDim = dim3(kThreads, 1, 1);
             cfg.dynamicSmemBytes = smem;
             int c = 0;  // the kernel's cluster shape (2 CTAs) is fixed at compile time
-            if (cudaOccupancyMaxActiveClusters(&c, k_gibbs_pair<false>, &cfg) == cudaSuccess && c > 0) n = c;
+            if (cudaOccupancyMaxActiveClusters(&c, k_gibbs_pair<false, 32>, &cfg) == cudaSuccess && c > 0) n = c;
         }
         (void)cudaGetLastError();
         g_max_clusters[dev] = n > 0 ? n : 1;
@@ -1497,6 +1489,25 @@ void fill_args(const bm_model_s *m, const bm_chains_s *c, int NC, int nsweeps, f
     a.tmem_cols = 2 * a.acc_stride;
     a.na = 0;
     a.nmma = 0;
+}
+
+// The shared-memory operand kernel for q rounded up to 8.
+template <bool BATCH>
+int launch_smem(int q, int grid, size_t smem, cudaStream_t st, const CUtensorMap &tm, const PairArgs &a,
+                const PairItem *items)
+{
+    auto go = [&](auto kern) -> int {
+        BM_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, kThreads, smem, st>>>(tm, a, items);
+        BM_CK_LAUNCH(BATCH ? "k_gibbs_pair (batch)" : "k_gibbs_pair");
+        return BM_OK;
+    };
+    switch ((q + 7) / 8) {
+    case 1: return go(k_gibbs_pair<BATCH, 8>);
+    case 2: return go(k_gibbs_pair<BATCH, 16>);
+    case 3: return go(k_gibbs_pair<BATCH, 24>);
+    default: return go(k_gibbs_pair<BATCH, 32>);
+    }
 }
 
 // The tensor-memory operand kernel for q rounded up to 8.
@@ -1617,12 +1628,9 @@ int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta,
     PairArgs a;
     fill_args(m, c, NC, nsweeps, beta, c->s, a);
     const size_t smem = smem_bytes(m, NC);
-    BM_CK(cudaFuncSetAttribute(k_gibbs_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nclusters = (c->M + NC - 1) / NC;
-    k_gibbs_pair<false><<<2 * nclusters, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(m->tmap_jp), a,
-                                                                nullptr);
-    BM_CK_LAUNCH("k_gibbs_pair");
-    return BM_OK;
+    return launch_smem<false>(a.q, 2 * nclusters, smem, st, *reinterpret_cast<const CUtensorMap *>(m->tmap_jp), a,
+                              nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1736,10 +1744,8 @@ int bm_pair_batch_sweep(bm_pair_batch_s *b, int nsweeps, float beta, cudaStream_
     }
     BM_CK(cudaMemcpyAsync(b->items_dev, b->items_host, (size_t)n * sizeof(PairItem), cudaMemcpyHostToDevice, st));
     BM_CK(cudaEventRecord(b->used, st));
-    BM_CK(cudaFuncSetAttribute(k_gibbs_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    k_gibbs_pair<true><<<2 * n, kThreads, b->smem, st>>>(b->items_host[0].tm, b->items_host[0].a, b->items_dev);
-    BM_CK_LAUNCH("k_gibbs_pair (batch)");
-    return BM_OK;
+    return launch_smem<true>(b->models[0]->q, 2 * n, b->smem, st, b->items_host[0].tm, b->items_host[0].a,
+                             b->items_dev);
 }
 
 int bm_pair_batch_autotune(bm_pair_batch_s *b, cudaStream_t st)
