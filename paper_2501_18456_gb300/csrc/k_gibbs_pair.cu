@@ -50,7 +50,9 @@
 //                lane quarters of a site's rows, add h and store them as one
 //                padded row per chain; each thread reads its row and the
 //                staged in-block coupling blocks (padded layout Jc, one bulk
-//                copy per block) with 128-bit loads, then draws;
+//                copy per block) with 128-bit loads, then draws (draw_symbol;
+//                the block's Philox numerators are computed while its
+//                accumulator fills);
 //   warps 7-11   generators of the one-hot operand tiles (2-slot ring), one
 //                thread per chain (zero the row, then store its few nonzeros).
 // Every wait is bounded by %globaltimer (2 s); a timeout sets the CTA's abort
@@ -317,10 +319,12 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Categorical draw from beta*log2(e)-scaled fields H[0..q) (entries q..QC
-// are -inf): weights 2^(H_a - max), prefix sums W_a, and the symbol is the
-// number of prefix sums <= u * W_{q-1}, capped at q-1; since the prefix sums
-// do not decrease this is the first a with u * W_{q-1} < W_a.
+// Categorical draw of the Gibbs conditional (Sec. 2.1) from beta*log2(e)-
+// scaled fields H[0..q) (entries q..QC are -inf): weights 2^(H_a - max) by
+// the hardware base-2 exponential (ex2.approx.ftz, a few ulp), prefix sums
+// W_a, and the symbol is the number of prefix sums <= u * W_{q-1}, capped at
+// q-1; since the prefix sums do not decrease this is the first a with
+// u * W_{q-1} < W_a.  u = r24 / 2^24 from the chain's Philox counter.
 template <int QC>
 __device__ __forceinline__ int draw_symbol(float (&H)[QC], int q, uint32_t r24)
 {
