@@ -198,6 +198,30 @@ def test_gibbs_long_sequences_teacher_forced(bm, orc, L, M, engine):
             assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
 
 
+@pytest.mark.parametrize("L,M", [(500, 200), (700, 150)])
+def test_gibbs_pair_small_alphabet_long_rows_teacher_forced(bm, orc, L, M):
+    """RNA alphabet at L = 500 and 700: the two-CTA sweep keeps the one-hot
+    operand in tensor memory there (K chunks <= 4x the 20 sites of a block),
+    and the state rows leave room for only 3 and 2 coupling-tile ring slots,
+    so the ring wraps every few chunks.  Two sweeps of sampled chains,
+    every site checked."""
+    h, J = synth.planted_local_model(L, 5, 19, sigma_h=1.0, sigma_J=0.3)
+    m = load(bm, h, J, "mma_pair")
+    c = bm.bm_chains_init(m, M, 41)
+    s0 = states_of(bm, c)
+    bm.bm_gibbs_sweep(m, c, 1, 1.0)
+    s1 = states_of(bm, c)
+    bm.bm_gibbs_sweep(m, c, 1, 1.0)
+    bm.bm_device_status(m)
+    s2 = states_of(bm, c)
+    h64, J64 = h.astype(np.float64), J.astype(np.float64)
+    sample = sorted(set(np.random.default_rng(4).choice(M, 24, replace=False).tolist()) | {M - 1})
+    for k in sample:
+        for sw, (a, b) in enumerate([(s0, s1), (s1, s2)]):
+            bad, worst, _ = orc.gibbs_verify(h64, J64, a[k:k + 1], b[k:k + 1], 41, sw, 1.0, k)
+            assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
+
+
 @pytest.mark.parametrize("L,q,M", [(900, 10, 160), (600, 16, 2000), (300, 32, 1500), (777, 21, 333)])
 @pytest.mark.parametrize("engine", ["mma", "mma_pair"])
 def test_gibbs_tensor_core_grid_teacher_forced(bm, orc, L, q, M, engine):
