@@ -121,9 +121,12 @@ int bm_potts_get(bm_model m, float *h, float *J, int where, void *stream);
 int bm_potts_set(bm_model m, const float *h, const float *J, int where, void *stream);
 
 /* Synchronise `stream` and report device-side errors recorded by earlier
- * kernels of this model (bounded waits that gave up): BM_OK, or
- * BM_ETIMEOUT (the error word is then cleared).  bm_update with a Pearson
- * request performs the same check. */
+ * kernels of this model, then clear them: BM_OK; BM_ETIMEOUT (a bounded
+ * wait gave up); BM_EINVAL (a scored sequence held a symbol >= q);
+ * BM_ENUMERIC (a coupling beyond the fp16 range, |J| > 65504, reached the
+ * fp16 split layout of the tensor-core sweep or fields: it was clamped and
+ * those results are invalid; the FP32 engine has no such limit).  bm_update
+ * with a Pearson request performs the timeout check. */
 int bm_device_status(bm_model m, void *stream);
 
 /* L and q of a model. */
@@ -249,6 +252,9 @@ int bm_seq_weights(const uint8_t *msa_dev, int N, int L, double seqid, float *w_
  *   N > BM_SEQ_WEIGHTS_STATIC_MAX_N -> BM_EINVAL (message names the limit).
  *   The first call on a device (with that device current) looks up the
  *   array's device address; make that first call before any stream capture.
+ *   The address is kept for the life of the process: after cudaDeviceReset
+ *   (which unloads the library's module with its array) this entry point
+ *   must not be called again on that device in the same process.
  *   Every call reuses the same array (its counters are cleared at the start
  *   of each call), so calls whose GPU work overlaps -- different streams or
  *   host threads -- race and must be serialised by the caller.

@@ -69,6 +69,8 @@ def _load():
         "orc_conditional": (None, [P, P, I, I, P, I, D, P]),
         "orc_gibbs": (None, [P, P, I, I, I, P, U64, U64, U64, I, D]),
         "orc_gibbs_verify": (ctypes.c_long, [P, P, I, I, I, P, P, U64, U64, U64, D, P, P]),
+        "orc_gibbs_verify_rec": (ctypes.c_long, [P, P, I, I, I, P, P, U64, U64, U64, D, P, P,
+                                                 ctypes.c_long, P, P, P, P, P]),
         "orc_chain_stats": (None, [P, I, I, I, P]),
         "orc_seq_weights": (None, [P, I, I, I, P, P]),
         "orc_data_stats": (None, [P, P, I, I, I, D, P, P]),
@@ -181,6 +183,30 @@ def gibbs_verify(h, J, before, after, seed: int, sweep: int, beta: float = 1.0, 
     bad = _load().orc_gibbs_verify(_p(h), _p(J), L, q, M, _p(b), _p(a), seed, chain0, sweep, beta,
                                    _p(mx), _p(mn))
     return int(bad), float(mx[0]), float(mn[0])
+
+
+def gibbs_flips(h, J, before, after, seed: int, sweep: int, beta: float = 1.0, chain0: int = 0,
+                cap: int = 4096):
+    """gibbs_verify with a record of every disagreement: returns
+    (n_bad, min_margin, flips), flips = list of dicts with the chain (global
+    index), site, oracle margin, symbol found and symbol the oracle draws
+    (the first `cap` disagreements)."""
+    h, J, L, q = _shape_hJ(h, J)
+    b = _u8(before)
+    a = _u8(after)
+    M = b.shape[0]
+    mx = np.zeros(1)
+    mn = np.zeros(1)
+    rc = np.zeros(cap, dtype=np.int64)
+    rs = np.zeros(cap, dtype=np.int32)
+    rm = np.zeros(cap, dtype=np.float64)
+    rg = np.zeros(cap, dtype=np.int32)
+    rw = np.zeros(cap, dtype=np.int32)
+    bad = _load().orc_gibbs_verify_rec(_p(h), _p(J), L, q, M, _p(b), _p(a), seed, chain0, sweep, beta,
+                                       _p(mx), _p(mn), cap, _p(rc), _p(rs), _p(rm), _p(rg), _p(rw))
+    flips = [{"chain": int(rc[k]) + chain0, "site": int(rs[k]), "margin": float(rm[k]),
+              "got": int(rg[k]), "want": int(rw[k])} for k in range(min(int(bad), cap))]
+    return int(bad), float(mn[0]), flips
 
 
 # --- statistics ------------------------------------------------------------

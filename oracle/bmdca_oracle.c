@@ -200,11 +200,16 @@ void orc_gibbs(const double *h, const double *J, int L, int q, int M, uint8_t *S
  * on -- draws with the same uniform and compares with after[i].
  * Returns the number of site-updates that disagree; *max_margin receives
  * the largest oracle margin among the disagreements (0 if none) and
- * *min_margin the smallest margin over all site-updates. */
-long orc_gibbs_verify(const double *h, const double *J, int L, int q, int M,
-                      const uint8_t *before, const uint8_t *after, uint64_t seed,
-                      uint64_t chain0, uint64_t sweep, double beta,
-                      double *max_margin, double *min_margin)
+ * *min_margin the smallest margin over all site-updates.  The first `cap`
+ * disagreements are recorded (chain index relative to `before`, site,
+ * oracle margin, symbol found, symbol the oracle draws) when the record
+ * arrays are given, so that every boundary flip can be reported. */
+long orc_gibbs_verify_rec(const double *h, const double *J, int L, int q, int M,
+                          const uint8_t *before, const uint8_t *after, uint64_t seed,
+                          uint64_t chain0, uint64_t sweep, double beta,
+                          double *max_margin, double *min_margin, long cap,
+                          int64_t *rec_chain, int32_t *rec_site, double *rec_margin,
+                          int32_t *rec_got, int32_t *rec_want)
 {
     double H[64];
     uint8_t *s = (uint8_t *)malloc((size_t)L);
@@ -221,6 +226,13 @@ long orc_gibbs_verify(const double *h, const double *J, int L, int q, int M,
             if (mg < mnm) mnm = mg;
             uint8_t got = after[(size_t)m * L + i];
             if (got != pick) {
+                if (bad < cap && rec_chain) {
+                    rec_chain[bad] = m;
+                    rec_site[bad] = i;
+                    rec_margin[bad] = mg;
+                    rec_got[bad] = got;
+                    rec_want[bad] = pick;
+                }
                 ++bad;
                 if (mg > mxm) mxm = mg;
             }
@@ -231,6 +243,15 @@ long orc_gibbs_verify(const double *h, const double *J, int L, int q, int M,
     if (max_margin) *max_margin = mxm;
     if (min_margin) *min_margin = mnm;
     return bad;
+}
+
+long orc_gibbs_verify(const double *h, const double *J, int L, int q, int M,
+                      const uint8_t *before, const uint8_t *after, uint64_t seed,
+                      uint64_t chain0, uint64_t sweep, double beta,
+                      double *max_margin, double *min_margin)
+{
+    return orc_gibbs_verify_rec(h, J, L, q, M, before, after, seed, chain0, sweep, beta,
+                                max_margin, min_margin, 0, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------

@@ -170,12 +170,15 @@ int bm_device_status(bm_model m, void *stream)
 {
     if (!m) return bm_fail(BM_EINVAL, "bm_device_status: NULL model");
     cudaStream_t st = (cudaStream_t)stream;
-    int word[2] = {0, 0};
-    BM_CK(cudaMemcpyAsync(word, m->dflags + 3, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int word[3] = {0, 0, 0};
+    BM_CK(cudaMemcpyAsync(word, m->dflags + 3, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     BM_CK(cudaStreamSynchronize(st));
-    if (word[0] || word[1]) BM_CK(cudaMemsetAsync(m->dflags + 3, 0, 2 * sizeof(int), st));
+    if (word[0] || word[1] || word[2]) BM_CK(cudaMemsetAsync(m->dflags + 3, 0, 3 * sizeof(int), st));
     if (word[0]) return bm_fail(BM_ETIMEOUT, "device wait timed out in a Gibbs launch (error word 0x%x)", word[0]);
     if (word[1]) return bm_fail(BM_EINVAL, "a scored sequence held a symbol >= q (it contributed nothing)");
+    if (word[2])
+        return bm_fail(BM_ENUMERIC, "a coupling exceeds the fp16 range (|J| > 65504) of the tensor-core "
+                                    "sweep and fp16 fields; their results are invalid (use BM_ENGINE_SIMT)");
     return BM_OK;
 }
 

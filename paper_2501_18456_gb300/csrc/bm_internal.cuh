@@ -50,7 +50,8 @@ struct bm_model_s {
     alignas(64) unsigned char tmap_bf1[128] = {};
     // Small device scratch for flags / reductions (owned).
     int *dflags = nullptr;       // [8] check words; [3] = device error bits (4: wait timeout);
-                                 // [4] = a scored sequence held a symbol >= q
+                                 // [4] = a scored sequence held a symbol >= q;
+                                 // [5] = |J| beyond fp16 range in the split layout
     double *dred = nullptr;      // reduction partials, capacity red_cap doubles
     size_t red_cap = 0;
     int num_sms = 0;

@@ -62,6 +62,8 @@
 // its loop, the producer waits (bounded) for its own copies, TMEM is
 // released and the chains are left unchanged.
 #include "bm_internal.cuh"
+
+#include <type_traits>
 #include "tc_common.cuh"
 
 #include <cuda.h>
@@ -653,9 +655,15 @@ __device__ __forceinline__ float from_t(__half v) { return __half2float(v); }
 __device__ __forceinline__ __nv_bfloat16 to_t(float v, __nv_bfloat16 *) { return __float2bfloat16_rn(v); }
 __device__ __forceinline__ float from_t(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+//
+// fp16 holds magnitudes up to 65504.  A coupling beyond that is clamped to
+// +-65504 (so the operands stay finite) and flagged in *ovf; the model's
+// status call then reports BM_ENUMERIC for the tensor-core sweep.
 template <typename T>
-__global__ void k_build_mma_layout(const float *__restrict__ J, T *__restrict__ jt, int L, int q, int Kp, int B, int nb)
+__global__ void k_build_mma_layout(const float *__restrict__ J, T *__restrict__ jt, int L, int q, int Kp, int B, int nb,
+                                   int *__restrict__ ovf)
 {
+    constexpr bool kHalf = sizeof(T) == 2 && std::is_same<T, __half>::value;
     const size_t rows = (size_t)nb * kRowsA, n = rows * Kp;
     const int Q = L * q;
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
@@ -667,6 +675,10 @@ __global__ void k_build_mma_layout(const float *__restrict__ J, T *__restrict__ 
         if (k < Q && pp < B && i < L) {
             const int j = k / q, b = k % q;
             v = J[(((size_t)i * L + j) * q + a) * q + b];
+        }
+        if (kHalf && !(fabsf(v) <= 65504.0f)) {
+            atomicOr(ovf, 1);
+            v = v != v ? 0.0f : copysignf(65504.0f, v);
         }
         const T vh = to_t(v, (T *)nullptr);
         const size_t o = r * (size_t)(2 * Kp) + (size_t)(k / kKC) * (2 * kKC) + (k % kKC);
@@ -777,9 +789,10 @@ int bm_split_prepare(bm_model_s *m, int bf16, cudaStream_t st)
     const size_t n = (size_t)rows * Kp;
     const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 64);
     if (bf16)
-        k_build_mma_layout<__nv_bfloat16><<<grid, 256, 0, st>>>(m->J, (__nv_bfloat16 *)*buf, m->L, m->q, Kp, B, nb);
+        k_build_mma_layout<__nv_bfloat16><<<grid, 256, 0, st>>>(m->J, (__nv_bfloat16 *)*buf, m->L, m->q, Kp, B, nb,
+                                                                 m->dflags + 5);
     else
-        k_build_mma_layout<__half><<<grid, 256, 0, st>>>(m->J, (__half *)*buf, m->L, m->q, Kp, B, nb);
+        k_build_mma_layout<__half><<<grid, 256, 0, st>>>(m->J, (__half *)*buf, m->L, m->q, Kp, B, nb, m->dflags + 5);
     BM_CK_LAUNCH("k_build_mma_layout");
     (bf16 ? m->bf_current : m->mma_current) = true;
     return BM_OK;

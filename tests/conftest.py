@@ -13,6 +13,14 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built libbmdca.so")
 
 
+def pytest_terminal_summary(terminalreporter):
+    import fliplog
+    if fliplog.CHECKED[0]:
+        terminalreporter.section("Gibbs boundary flips")
+        for line in fliplog.summary_lines():
+            terminalreporter.write_line(line)
+
+
 @pytest.fixture(scope="session")
 def orc():
     import oracle

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 import torch
 
+import fliplog
 from paper_2501_18456_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -131,8 +132,8 @@ def test_tensor_core_batch_matches_oracle_and_per_model_sweeps(bm, orc, q):
         assert bm.bm_chains_sweep_counter(c) == 1
         pick = sorted(set(rng.choice(c.M, min(c.M, 12), replace=False).tolist()) | {c.M - 1})
         for k in pick:
-            bad, worst, _ = orc.gibbs_verify(h.astype(np.float64), J.astype(np.float64), s0[k:k + 1],
-                                             s1[k:k + 1], 200 + TC_SHAPES.index((m.L, c.M)), 0, 1.0, k)
+            bad, worst = fliplog.verify(orc, h, J, s0[k:k + 1], s1[k:k + 1],
+                                        200 + TC_SHAPES.index((m.L, c.M)), 0, 1.0, k, f"batch L={m.L}")
             assert bad == 0 or worst < 1e-5, (m.L, k, bad, worst)
     # continue: batch vs the same chains swept per model
     ref_mh, ref_c = build_tc(bm, engine=bm.BM_ENGINE_MMA_PAIR, q=q)

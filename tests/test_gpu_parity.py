@@ -17,11 +17,11 @@ import numpy as np
 import pytest
 import torch
 
+import fliplog
+from fliplog import FLIP_MARGIN
 from paper_2501_18456_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-
-FLIP_MARGIN = 1e-5
 DEV = "cuda"
 
 
@@ -47,9 +47,15 @@ def states_of(bm, c):
     return out.cpu().numpy()
 
 
+def here():
+    import os
+    return os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+
+
 def check_sweep(orc, h, J, before, after, seed, sweep, beta=1.0, chain0=0):
-    bad, worst, _ = orc.gibbs_verify(h.astype(np.float64), J.astype(np.float64), before, after,
-                                     seed, sweep, beta, chain0)
+    """Teacher-forced check of every site-update of one sweep; each flip is
+    logged (chain, site, margin) in the run's flip record."""
+    bad, worst = fliplog.verify(orc, h, J, before, after, seed, sweep, beta, chain0, here())
     assert bad == 0 or worst < FLIP_MARGIN, f"{bad} disagreeing draws, worst margin {worst}"
     assert bad <= max(2, before.size // 10000), f"too many boundary flips: {bad}"
     return bad
@@ -140,17 +146,28 @@ def test_gibbs_multi_sweep_call_equals_single_calls(bm, engine):
 @pytest.mark.parametrize("engine", GIBBS_ENGINES)
 def test_gibbs_free_run_matches_oracle(bm, orc, engine):
     """Three free-running sweeps: chains whose every draw is far from a CDF
-    boundary are identical to the oracle's."""
+    boundary are identical to the oracle's own free run.  Each sweep is also
+    checked teacher-forced, so every chain that left the oracle's trajectory
+    is accounted for by a logged boundary flip (chain, site, margin)."""
     L, q, M = 16, 21, 256
     h, J = synth.planted_local_model(L, q, 9)
     m = load(bm, h, J, engine)
     c = bm.bm_chains_init(m, M, 10)
     s0 = states_of(bm, c)
-    bm.bm_gibbs_sweep(m, c, 3, 1.0)
-    got = states_of(bm, c)
+    traj = [s0]
+    for _ in range(3):  # one sweep per call equals one 3-sweep call (tested above)
+        bm.bm_gibbs_sweep(m, c, 1, 1.0)
+        traj.append(states_of(bm, c))
+    got = traj[-1]
+    flipped = set()
+    for k in range(3):
+        n0 = len(fliplog.FLIPS)
+        check_sweep(orc, h, J, traj[k], traj[k + 1], 10, k)
+        flipped |= {f["chain"] for f in fliplog.FLIPS[n0:]}
     want = orc.gibbs(h.astype(np.float64), J.astype(np.float64), s0, 10, 0, 3)
-    same = (got == want).all(axis=1).mean()
-    assert same > 0.99
+    differ = set(np.nonzero((got != want).any(axis=1))[0].tolist())
+    assert differ <= flipped, f"chains off the oracle's trajectory without a logged flip: {differ - flipped}"
+    assert len(differ) < 0.01 * M
 
 
 @pytest.mark.parametrize("engine", GIBBS_ENGINES)
@@ -170,7 +187,7 @@ def test_gibbs_config2_launch_sampled_chains(bm, orc, engine):
     sample = sorted(set(rng.choice(M, 24, replace=False).tolist()) | {0, 65, 66, 79, 80, 143, 144, M - 1})
     h64, J64 = h.astype(np.float64), J.astype(np.float64)
     for k in sample:
-        bad, worst, _ = orc.gibbs_verify(h64, J64, s0[k:k + 1], s1[k:k + 1], 2024, 0, 1.0, k)
+        bad, worst = fliplog.verify(orc, h64, J64, s0[k:k + 1], s1[k:k + 1], 2024, 0, 1.0, k, here())
         assert bad == 0 or worst < FLIP_MARGIN, (k, bad, worst)
 
 
@@ -194,7 +211,7 @@ def test_gibbs_long_sequences_teacher_forced(bm, orc, L, M, engine):
     sample = sorted(set(np.random.default_rng(2).choice(M, min(M, 40), replace=False).tolist()) | {M - 1})
     for k in sample:
         for sw, (a, b) in enumerate([(s0, s1), (s1, s2)]):
-            bad, worst, _ = orc.gibbs_verify(h64, J64, a[k:k + 1], b[k:k + 1], 31, sw, 1.0, k)
+            bad, worst = fliplog.verify(orc, h64, J64, a[k:k + 1], b[k:k + 1], 31, sw, 1.0, k, here())
             assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
 
 
@@ -218,7 +235,7 @@ def test_gibbs_pair_small_alphabet_long_rows_teacher_forced(bm, orc, L, M):
     sample = sorted(set(np.random.default_rng(4).choice(M, 24, replace=False).tolist()) | {M - 1})
     for k in sample:
         for sw, (a, b) in enumerate([(s0, s1), (s1, s2)]):
-            bad, worst, _ = orc.gibbs_verify(h64, J64, a[k:k + 1], b[k:k + 1], 41, sw, 1.0, k)
+            bad, worst = fliplog.verify(orc, h64, J64, a[k:k + 1], b[k:k + 1], 41, sw, 1.0, k, here())
             assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
 
 
@@ -243,7 +260,7 @@ def test_gibbs_tensor_core_grid_teacher_forced(bm, orc, L, q, M, engine):
     sample = sorted(set(np.random.default_rng(3).choice(M, min(M, 14), replace=False).tolist()) | {0, M - 1})
     for k in sample:
         for sw, (a, b) in enumerate([(s0, s1), (s1, s2)]):
-            bad, worst, _ = orc.gibbs_verify(h64, J64, a[k:k + 1], b[k:k + 1], 41, sw, 1.0, k)
+            bad, worst = fliplog.verify(orc, h64, J64, a[k:k + 1], b[k:k + 1], 41, sw, 1.0, k, here())
             assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
 
 
@@ -267,7 +284,7 @@ def test_gibbs_more_chains_than_one_wave(bm, orc, engine):
     h64, J64 = h.astype(np.float64), J.astype(np.float64)
     for k in sample:
         for sw, (a, b) in enumerate([(s0, s1), (s1, s2)]):
-            bad, worst, _ = orc.gibbs_verify(h64, J64, a[k:k + 1], b[k:k + 1], 77, sw, 1.0, k)
+            bad, worst = fliplog.verify(orc, h64, J64, a[k:k + 1], b[k:k + 1], 77, sw, 1.0, k, here())
             assert bad == 0 or worst < FLIP_MARGIN, (k, sw, bad, worst)
 
 
@@ -310,6 +327,27 @@ def test_potts_load_checks(bm):
     bm.bm_potts_get(m, hh, JJ)
     torch.cuda.synchronize()
     assert np.array_equal(hh.numpy(), h) and np.array_equal(JJ.numpy(), J)
+
+
+@pytest.mark.parametrize("engine", ["mma", "mma_pair"])
+def test_coupling_beyond_fp16_range_is_reported(bm, engine):
+    """The tensor-core sweep holds J as fp16 hi + lo.  A coupling above the
+    fp16 range is clamped (operands stay finite) and reported as
+    BM_ENUMERIC by the status call; the FP32 engine takes the same model."""
+    L, q, M = 8, 4, 64
+    h, J = synth.planted_local_model(L, q, 3)
+    J[1, 2, 0, 1] = J[2, 1, 1, 0] = 1.0e5
+    m = load(bm, h, J, engine)
+    c = bm.bm_chains_init(m, M, 1)
+    bm.bm_gibbs_sweep(m, c, 1, 1.0)
+    with pytest.raises(bm.BmError) as e:
+        bm.bm_device_status(m)
+    assert e.value.code == bm.BM_ENUMERIC
+    bm.bm_device_status(m)  # cleared
+    m2 = load(bm, h, J, "simt")
+    c2 = bm.bm_chains_init(m2, M, 1)
+    bm.bm_gibbs_sweep(m2, c2, 1, 1.0)
+    bm.bm_device_status(m2)
 
 
 # ---------------------------------------------------------------- chain_stats

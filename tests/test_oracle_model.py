@@ -202,3 +202,22 @@ def test_gibbs_verify_accepts_oracle_and_rejects_planted_error(orc):
     assert orc.gibbs_verify(h, J, s0, wrong, seed=4, sweep=5)[0] >= 1
     # a different sweep word gives different uniforms
     assert orc.gibbs_verify(h, J, s0, s1, seed=4, sweep=6)[0] > 0
+
+
+def test_gibbs_flips_records_the_planted_disagreement(orc):
+    """The flip record names the chain (global index), the site, the symbol
+    found and the oracle's own draw of the first disagreement."""
+    L, q = 8, 6
+    h, J = random_model(L, q, 61)
+    s0 = orc.chains_init(40, L, q, 4, chain0=100)
+    s1 = orc.gibbs(h, J, s0, seed=4, sweep0=5, nsweeps=1, chain0=100)
+    bad, mn, flips = orc.gibbs_flips(h, J, s0, s1, seed=4, sweep=5, chain0=100)
+    assert bad == 0 and flips == [] and mn > 0
+    wrong = s1.copy()
+    wrong[3, 2] = (s1[3, 2] + 1) % q
+    bad, _, flips = orc.gibbs_flips(h, J, s0, wrong, seed=4, sweep=5, chain0=100)
+    assert bad >= 1
+    first = flips[0]
+    assert (first["chain"], first["site"]) == (103, 2)
+    assert first["got"] == wrong[3, 2] and first["want"] == s1[3, 2]
+    assert bad == orc.gibbs_verify(h, J, s0, wrong, seed=4, sweep=5, chain0=100)[0]
