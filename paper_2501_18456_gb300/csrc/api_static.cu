@@ -14,7 +14,9 @@
 // it names a host-side stand-in), so the first call on each device, with
 // that device current, looks the address up with cudaGetSymbolAddress and
 // caches it.  That first call should therefore happen before any stream
-// capture begins.  All calls share the one array: calls whose work overlaps
+// capture begins.  The cached address lives as long as the process; a
+// cudaDeviceReset unloads the module and with it the array, so the entry
+// point must not be used on that device again afterwards.  All calls share the one array: calls whose work overlaps
 // on the GPU (different streams, or different host threads) race on it.
 // The counters are cleared at the start of every call.
 #include "bm_internal.cuh"

@@ -3,9 +3,16 @@
 Callers that cannot allocate device memory (another framework's caching
 allocator holds it, or a serving loop must not enter the driver allocator)
 use this entry point; its scratch is a fixed array inside the library.  The
-test calls it through the C ABI and checks that its weights and M_eff equal
-those of bm_seq_weights (the same exact tolerance the weight tests use),
-on two calls in a row so that stale scratch from the first call would show.
+tests call it through the C ABI and check
+  * its weights and M_eff against the FP64 oracle's seq_weights (Eq. 7;
+    bit-exact, as the weight parity tests require) and against the
+    allocating entry point bm_seq_weights;
+  * shapes that span several 256-symbol chunks of its identity kernel
+    (L = 300) and sequence counts that are not multiples of 64;
+  * two calls in a row, the second over the first call's stale scratch;
+  * that a call allocates nothing: the device's free memory and torch's
+    allocator figures are unchanged across calls after the first (which
+    may load the library's module and with it the array).
 This file is named to be collected last.
 """
 import ctypes
@@ -18,6 +25,8 @@ from paper_2501_18456_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
+CASES = [(3000, 96, 1), (777, 130, 2), (1001, 300, 3), (65, 513, 4)]
+
 
 def _call_static(lib, msa, w, seqid):
     meff = ctypes.c_double()
@@ -28,21 +37,45 @@ def _call_static(lib, msa, w, seqid):
     return rc, meff.value
 
 
-def test_static_scratch_weights_match_allocating_entry_point(bm):
+def test_static_scratch_weights_match_oracle_and_allocating_entry_point(bm, orc):
     lib = bm.lib()
-    for N, L, seed in [(3000, 96, 1), (777, 130, 2)]:  # second call: smaller N over stale scratch
-        X = torch.from_numpy(synth.clustered_msa(N, L, 21, seed, n_ancestors=N // 8)).cuda()
+    for N, L, seed in CASES:  # later calls: other N and L over stale scratch
+        msa = synth.clustered_msa(N, L, 21, seed, n_ancestors=max(1, N // 8))
+        X = torch.from_numpy(msa).cuda()
+        w_o, meff_o = orc.seq_weights(msa, 0.8)
         w_ref = torch.empty(N, dtype=torch.float32, device="cuda")
         meff_ref = bm.bm_seq_weights(X, w_ref, 0.8)
         w = torch.full((N,), -1.0, dtype=torch.float32, device="cuda")
         rc, meff = _call_static(lib, X, w, 0.8)
         assert rc == 0, lib.bm_last_error()
         torch.cuda.synchronize()
+        # weights are 1/N_m of an exact integer count: FP32 of the oracle's FP64
+        assert np.array_equal(w.cpu().numpy(), w_o.astype(np.float32)), (N, L)
+        assert abs(meff - meff_o) <= 1e-9 * meff_o, (N, L, meff, meff_o)
         assert torch.equal(w, w_ref)
         assert meff == meff_ref
         rc, meff2 = _call_static(lib, X, w, 0.8)  # repeat on the same inputs
         assert rc == 0 and meff2 == meff_ref
         assert torch.equal(w, w_ref)
+
+
+def test_static_scratch_allocates_nothing(bm):
+    lib = bm.lib()
+    N, L = 2000, 120
+    X = torch.from_numpy(synth.clustered_msa(N, L, 21, 9, n_ancestors=250)).cuda()
+    w = torch.empty(N, dtype=torch.float32, device="cuda")
+    rc, _ = _call_static(lib, X, w, 0.8)  # first call on the device: set-up
+    assert rc == 0, lib.bm_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0, res0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(3):
+        rc, _ = _call_static(lib, X, w, 0.8)
+        assert rc == 0, lib.bm_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"device free memory changed by {free0 - free1} bytes"
+    assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == res0
 
 
 def test_static_scratch_rejects_oversize(bm):
