@@ -63,9 +63,12 @@ def request_stream(models, rate: float, duration: float, seed: int):
 
 
 def run_stream(models, rate: float = 10.0, duration: float = 8.0, seed: int = 1, slots: int = 16,
-               budget_bytes: int = 8 << 30, engine: int | None = None) -> dict:
+               budget_bytes: int = 8 << 30, engine: int | None = None, burst: bool = False) -> dict:
     """Runs the request stream through a fresh server; returns its statistics.
-    engine: a BM_ENGINE_* value applied to every model before it is served."""
+    engine: a BM_ENGINE_* value applied to every model before it is served.
+    burst: submit every request of the stream at once (arrival times
+    ignored), so the figures are those of a saturated server: sequences/s is
+    then its capacity rather than the offered load."""
     if engine is not None:
         for m in models:
             bmdca.bm_model_set_engine(m, engine)
@@ -101,7 +104,7 @@ def run_stream(models, rate: float = 10.0, duration: float = 8.0, seed: int = 1,
     t0 = time.perf_counter()
     for (ta, kind, mi, n, sweeps, beta, rseed) in stream:
         delay = ta - (time.perf_counter() - t0)
-        if delay > 0:
+        if delay > 0 and not burst:
             time.sleep(delay)
         m = models[mi]
         if kind == bmdca.BM_REQ_SAMPLE:
@@ -127,8 +130,26 @@ def run_stream(models, rate: float = 10.0, duration: float = 8.0, seed: int = 1,
         raise RuntimeError(f"{len(errors)} serving requests failed: {sorted(set(errors))}")
     return {"requests": int(st["completed"]), "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "mean_ms": st["mean_ms"], "sequences_per_s": st["sequences"] / max(st["span_s"], 1e-9),
-            "max_running": int(st["max_running"]), "offered_rate_per_s": rate, "duration_s": duration,
-            "wall_s": wall, "slots": slots, "budget_bytes": int(budget_bytes)}
+            "max_running": int(st["max_running"]), "offered_rate_per_s": None if burst else rate,
+            "duration_s": duration, "wall_s": wall, "slots": slots, "budget_bytes": int(budget_bytes),
+            "burst": burst, "seed": seed}
+
+
+def run_seeds(models, rate: float, requests: int, seeds, engine: int | None = None, **kw) -> dict:
+    """The Poisson stream for several seeds (about requests/len(seeds)
+    requests each): per-seed results and the spread of p50 / p99."""
+    per = max(1, requests // len(seeds))
+    runs = [run_stream(models, rate, per / rate, sd, engine=engine, **kw) for sd in seeds]
+    p50 = [r["p50_ms"] for r in runs]
+    p99 = [r["p99_ms"] for r in runs]
+    return {"requests": sum(r["requests"] for r in runs), "seeds": list(seeds),
+            "p50_ms": float(np.median(p50)), "p50_ms_range": [min(p50), max(p50)],
+            "p99_ms": float(np.median(p99)), "p99_ms_range": [min(p99), max(p99)],
+            "mean_ms": float(np.mean([r["mean_ms"] for r in runs])),
+            "sequences_per_s": float(np.mean([r["sequences_per_s"] for r in runs])),
+            "max_running": max(r["max_running"] for r in runs), "offered_rate_per_s": rate,
+            "per_seed": [{k: r[k] for k in ("seed", "requests", "p50_ms", "p99_ms", "sequences_per_s")}
+                         for r in runs]}
 
 
 def main():

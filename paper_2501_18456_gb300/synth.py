@@ -19,6 +19,10 @@ proteins, q = 5 for RNA/DNA, gap = symbol 0):
                          resampling a per-descendant fraction of sites, so
                          close relatives exceed 80% identity and sequence
                          reweighting matters
+  cluster_mix            the same clustering over given sequences: each of N
+                         descendants copies ancestor k mod n_anc and takes a
+                         per-descendant U[lo, hi] fraction of its sites from
+                         its own donor sequence (a random selection only)
 """
 from __future__ import annotations
 
@@ -105,4 +109,19 @@ def clustered_msa(N: int, L: int, q: int, seed: int, n_ancestors: int | None = N
     mask = rng.random((N, L)) < rate
     fresh = sample_sites(N)
     X[mask] = fresh[mask]
+    return X[rng.permutation(N)]
+
+
+def cluster_mix(ancestors: np.ndarray, donors: np.ndarray, seed: int, resample_lo: float = 0.02,
+                resample_hi: float = 0.3) -> np.ndarray:
+    """Descendant m = ancestors[m % n_anc] with a U[lo, hi] fraction of its
+    sites (chosen at random) replaced by donors[m]; rows shuffled."""
+    rng = _rng(seed, 6)
+    anc = np.ascontiguousarray(ancestors, dtype=np.uint8)
+    don = np.ascontiguousarray(donors, dtype=np.uint8)
+    N, L = don.shape
+    X = anc[np.arange(N) % anc.shape[0]].copy()
+    rate = rng.uniform(resample_lo, resample_hi, size=(N, 1))
+    mask = rng.random((N, L)) < rate
+    X[mask] = don[mask]
     return X[rng.permutation(N)]

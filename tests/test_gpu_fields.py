@@ -43,7 +43,8 @@ def abs_scale(h, J, S):
     aJ = np.abs(J.astype(np.float64))
     out = np.empty((S.shape[0],) + h.shape)
     for k in range(S.shape[0]):
-        out[k] = np.abs(h) + aJ[:, np.arange(L), :, S[k]].sum(axis=1)
+        # aJ[:, j, :, s_j] over j has shape (j, i, a): sum over j
+        out[k] = np.abs(h) + aJ[:, np.arange(L), :, S[k]].sum(axis=0)
     return out
 
 
