@@ -84,7 +84,11 @@ enum {
                                are exchanged through distributed shared memory.  Where a
                                block's K chunks number at most 4x its sites, the one-hot
                                states are the MMA's A operand in tensor memory (128 chains
-                               per cluster, one per TMEM lane) and J the B operand */
+                               per cluster, one per TMEM lane) and J the B operand */,
+    BM_ENGINE_MMA_PAIR2 = 4 /* the two-CTA form with the two SMs' tensor cores paired
+                               (tcgen05 cta_group::2): one MMA of M = 256 rows covers both
+                               CTAs' site blocks, and each CTA generates and holds the
+                               one-hot rows of half of the cluster's chains */
 };
 
 /* Library version string, e.g. "bmdca-gb300 0.1". */

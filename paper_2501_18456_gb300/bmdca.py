@@ -20,7 +20,7 @@ _lib = None
 BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ENUMERIC, BM_ETIMEOUT, BM_EDEVICE, BM_EBUSY = (
     0, -1, -2, -3, -4, -5, -6, -7)
 BM_HOST, BM_DEVICE = 0, 1
-BM_ENGINE_SIMT, BM_ENGINE_AUTO, BM_ENGINE_MMA, BM_ENGINE_MMA_PAIR = 0, 1, 2, 3
+BM_ENGINE_SIMT, BM_ENGINE_AUTO, BM_ENGINE_MMA, BM_ENGINE_MMA_PAIR, BM_ENGINE_MMA_PAIR2 = 0, 1, 2, 3, 4
 BM_STATS_AUTO, BM_STATS_SIMT, BM_STATS_MMA_BF16, BM_STATS_MMA_FP8 = 0, 1, 2, 3
 BM_FIELDS_FP32, BM_FIELDS_FP16X2, BM_FIELDS_BF16X2 = 0, 1, 2
 BM_REQ_SAMPLE, BM_REQ_SCORE, BM_REQ_SCAN = 1, 2, 3

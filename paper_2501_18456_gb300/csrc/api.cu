@@ -194,7 +194,7 @@ int bm_model_set_engine(bm_model m, int engine)
 {
     if (!m) return bm_fail(BM_EINVAL, "bm_model_set_engine: NULL model");
     if (engine != BM_ENGINE_SIMT && engine != BM_ENGINE_AUTO && engine != BM_ENGINE_MMA &&
-        engine != BM_ENGINE_MMA_PAIR)
+        engine != BM_ENGINE_MMA_PAIR && engine != BM_ENGINE_MMA_PAIR2)
         return bm_fail(BM_EINVAL, "bm_model_set_engine: unknown engine %d", engine);
     m->engine = engine;
     return BM_OK;
@@ -204,7 +204,10 @@ int bm_model_sweep_engine(bm_model m, int M, int *engine_out)
 {
     if (!m || !engine_out || M < 1) return bm_fail(BM_EINVAL, "bm_model_sweep_engine: bad argument");
     const int form = bm_sweep_form(m, M);
-    *engine_out = form == 2 ? BM_ENGINE_MMA_PAIR : form == 1 ? BM_ENGINE_MMA : BM_ENGINE_SIMT;
+    *engine_out = form == 3   ? BM_ENGINE_MMA_PAIR2
+                  : form == 2 ? BM_ENGINE_MMA_PAIR
+                  : form == 1 ? BM_ENGINE_MMA
+                              : BM_ENGINE_SIMT;
     return BM_OK;
 }
 
@@ -378,6 +381,7 @@ static bool tensor_beats_gather(int L, int q, int M)
 
 int bm_sweep_form(const bm_model_s *m, int M)
 {
+    if (m->engine == BM_ENGINE_MMA_PAIR2) return 3;
     if (m->engine == BM_ENGINE_MMA_PAIR) return 2;
     if (m->engine == BM_ENGINE_MMA) return 1;
     if (m->engine != BM_ENGINE_AUTO) return 0;
@@ -411,7 +415,8 @@ int bm_sweep_run(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStr
     const int form = bm_sweep_form(m, c->M);
     for (int done = 0; done < nsweeps;) {
         const int k = nsweeps - done < kMaxSweepsPerLaunch ? nsweeps - done : kMaxSweepsPerLaunch;
-        const int rc = form == 2   ? bm_launch_gibbs_pair(m, c, k, beta, st)
+        const int rc = form == 3   ? bm_launch_gibbs_paired(m, c, k, beta, st)
+                       : form == 2 ? bm_launch_gibbs_pair(m, c, k, beta, st)
                        : form == 1 ? bm_launch_gibbs_mma(m, c, k, beta, st)
                                    : bm_launch_gibbs_simt(m, c, k, beta, st);
         if (rc != BM_OK) return rc;

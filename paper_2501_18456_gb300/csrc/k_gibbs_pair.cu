@@ -80,6 +80,8 @@ namespace {
 
 constexpr int kNA = 3;                  // coupling ring slots
 constexpr int kNB = 2;                  // one-hot ring slots (NC x 128 bytes each)
+constexpr int kNB2 = 3;                 // the same with paired tensor cores (NC/2 x 128 bytes each)
+static_assert(kNB <= kNA && kNB2 <= kNA, "one-hot slots are freed through the coupling ring's barriers");
 constexpr int kKC = 64;                 // fp16 K elements per chunk (128-byte rows)
 constexpr int kRowsA = 128;             // MMA M
 constexpr int kTileA = kRowsA * 128;    // one hi or lo tile (16 KB)
@@ -91,7 +93,7 @@ constexpr int kDraw = 32 * kDrawWarps;  // drawer threads
 constexpr int kGen = 32 * kGenWarps;    // generator threads
 constexpr int kThreads = 64 + kDraw + kGen;
 constexpr int kNCmax = 160;
-constexpr int kNBars = 2 * kNA + 2 * kNB + 2 + 2 + 2 + 1 + 1 + 1;
+constexpr int kNBars = 2 * kNA + 2 * kNB2 + 2 + 2 + 2 + 1 + 1 + 1 + kNA + 1;
 
 // ---------------------------------------------------------------- cluster helpers
 __device__ __forceinline__ uint32_t cluster_rank()
@@ -124,6 +126,15 @@ __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t a)
 __device__ __forceinline__ void mbar_arrive_peer(uint32_t a)
 {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+// Remote arrival without release semantics (about 10x cheaper for the issuing
+// thread).  Used only to relay a completion the thread has already observed
+// on its own CTA's barrier (TMA bytes landed; generator stores fenced for the
+// async proxy and arrived with release), so the relayed data is in place.
+__device__ __forceinline__ void mbar_arrive_peer_relaxed(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(a) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_cl(uint32_t bar, uint32_t parity)
@@ -210,19 +221,21 @@ struct Smem {
     uint32_t a, b, hs, st, snap, corr, hrow, jtab, bars, misc, total;
 };
 
-__host__ __device__ inline Smem smem_layout(int NC, int Lp, int B, int nK, int q)
+// nrows_b: one-hot operand rows per CTA (NC, or NC/2 when the two CTAs'
+// tensor cores are paired and each holds half of the chains' rows).
+__host__ __device__ inline Smem smem_layout(int NC, int Lp, int B, int nK, int q, int nrows_b)
 {
     Smem s;
     s.a = 0;
     s.b = s.a + kNA * kSlotA;
-    s.hs = s.b + kNB * NC * 128;
+    s.hs = s.b + (nrows_b < NC ? kNB2 : kNB) * nrows_b * 128;
     s.st = s.hs + NC * hs_stride(q) * 4;          // fields h + G of one site: [chain][a]
     s.snap = s.st + NC * st_stride(Lp);           // [2 pair slots][2 blocks][NC][snap_stride]
     s.corr = (s.snap + 4 * NC * snap_stride(B) + 15) & ~15u;
     s.hrow = s.corr + (uint32_t)corr_slots(B) * q * q4_of(q) * 4;
     s.jtab = s.hrow + kRowsA * 4;
-    s.bars = (s.jtab + nK * 4 + 15) & ~15u;
-    s.misc = s.bars + kNBars * 8;
+    s.bars = (s.jtab + nK * 8 + 15) & ~15u;  // jtab: per chunk, first and last site of each 32-column half
+    s.misc = s.bars + kNBars * 8;  // TMEM address, abort flag
     s.total = s.misc + 16;
     return s;
 }
@@ -312,6 +325,96 @@ __device__ Seg seg_info(const PairArgs &p, long long P, int step, int r)
     return s;
 }
 
+// Paired tensor cores (cta_group::2): one MMA stream serves both CTAs, so
+// both run the same chunk sequence.  Step s of pair P has the chunks of the
+// form above, in both CTAs: A and C the main chunks of pair P, B the delta
+// chunks of block 2P-2, D those of blocks 2P-2 and 2P-1.  Per CTA r: the
+// coupling rows it loads (block t; CTA 0's step B loads the rows of block
+// 2P-2, whose accumulator is already drawn, and the MMA's CTA-0 half lands
+// there harmlessly), the accumulator slot (jd & 1), what its generators wait
+// for, and which CTAs' accumulators are complete after the step (bit r of
+// commit_mask).  Blocks past the end (an odd block count) get the rows of a
+// valid block and results nobody reads.
+struct SegCg {
+    Seg s;
+    long long jd;
+    int commit_mask;
+};
+
+__device__ SegCg seg_info_cg(const PairArgs &p, long long P, int step, int r)
+{
+    SegCg g;
+    Seg &s = g.s;
+    s.n = s.n0 = s.c0 = s.c1 = s.wait_kind = 0;
+    s.delta = false;
+    s.t = s.wait_kb = s.commit_kb = s.d0 = s.d1 = -1;
+    g.jd = P;
+    g.commit_mask = 0;
+    if (step == 0 || step == 2) {
+        if (2 * P >= p.nblocks) return g;
+        s.c0 = step == 0 ? 0 : p.X;
+        s.n = s.n0 = step == 0 ? p.X : p.nK - p.X;
+        s.t = 2 * P + r;
+        if (step == 2 && P == 0) g.commit_mask = 1;
+        return g;
+    }
+    if (P < 1) return g;
+    s.delta = true;
+    if (step == 1) {
+        if (2 * P - 1 >= p.nblocks) return g;
+        int lo, hi;
+        blk_chunks(p, 2 * P - 2, lo, hi);
+        s.c0 = lo;
+        s.n = s.n0 = hi - lo + 1;
+        s.t = r == 1 ? 2 * P - 1 : 2 * P - 2;
+        s.d0 = 2 * P - 2;
+        s.wait_kb = 2 * P - 2;
+        s.wait_kind = 1;
+        g.jd = P - 1;
+        g.commit_mask = 2;
+        return g;
+    }
+    if (2 * P >= p.nblocks) return g;
+    int a0, a1, c0, c1;
+    blk_chunks(p, 2 * P - 2, a0, a1);
+    blk_chunks(p, 2 * P - 1, c0, c1);
+    if (c0 <= a1 + 1 && a0 <= c1 + 1) {
+        s.c0 = min(a0, c0);
+        s.n = s.n0 = max(a1, c1) - s.c0 + 1;
+    } else {  // the two blocks wrap around the end of a sweep
+        s.c0 = a0;
+        s.n0 = a1 - a0 + 1;
+        s.c1 = c0;
+        s.n = s.n0 + (c1 - c0 + 1);
+    }
+    s.t = 2 * P + r;
+    s.d0 = 2 * P - 2;
+    s.d1 = 2 * P - 1;
+    s.wait_kb = 2 * P - 1;
+    s.wait_kind = r == 0 ? 2 : 1;
+    g.commit_mask = 1;
+    return g;
+}
+
+// tcgen05 forms for the paired tensor cores of a CTA pair.
+__device__ __forceinline__ void mma_f16_cg2(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// Arrive (once) on the barrier at shared offset `bar` of every CTA in `mask`
+// when all MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -354,7 +457,15 @@ __device__ __forceinline__ int draw_symbol(float (&H)[QC], int q, uint32_t r24)
 
 // BATCH: cluster k runs items[k] (its own model, tensor map and chain tile);
 // otherwise every cluster runs the launch arguments on chains k*NC ...
-template <bool BATCH, int QC>
+// CG2: the two CTAs' tensor cores are paired (tcgen05 cta_group::2): CTA 0
+// issues every MMA for both (M = 256: the coupling rows of block 2P in CTA 0
+// and of block 2P+1 in CTA 1; N = NC chains, whose one-hot rows are split
+// between the CTAs: CTA r generates and holds chains [r NC/2, (r+1) NC/2)).
+// Each SM then generates and reads half of the one-hot operand per chunk.
+// CTA 1's generators and drawers arrive on CTA 0's barriers; CTA 1's coupling
+// tiles are reported to CTA 0 by a forwarding thread; CTA 0's commits
+// multicast to both CTAs.
+template <bool BATCH, int QC, bool CG2>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_gibbs_pair(const __grid_constant__ CUtensorMap tm_one, const __grid_constant__ PairArgs p_one,
                  const PairItem *__restrict__ items)
@@ -365,7 +476,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = su32(smem_raw);
     unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    const Smem lay = smem_layout(p.NC, p.Lp, p.B, p.nK, p.q);
+    const int NCg = CG2 ? p.NC / 2 : p.NC;  // one-hot operand rows of this CTA
+    const Smem lay = smem_layout(p.NC, p.Lp, p.B, p.nK, p.q, NCg);
     float *Hs = reinterpret_cast<float *>(base + lay.hs);
     uint8_t *st = base + lay.st;
     uint8_t *snap = base + lay.snap;
@@ -376,13 +488,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + lay.misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(base + lay.misc + 4);
     const uint32_t full_a = su32(bars), empty_a = full_a + 8 * kNA;
-    const uint32_t full_b = empty_a + 8 * kNA, empty_b = full_b + 8 * kNB;
-    const uint32_t acc_full = empty_b + 8 * kNB;  // [2], own block j = kb/2 in slot j % 2
+    constexpr int NB = CG2 ? kNB2 : kNB;  // one-hot ring slots
+    const uint32_t full_b = empty_a + 8 * kNA, empty_b = full_b + 8 * kNB2;
+    const uint32_t acc_full = empty_b + 8 * kNB2;  // [2], own block j = kb/2 in slot j % 2
     const uint32_t acc_empty = acc_full + 16;     // [2]
     const uint32_t ready = acc_empty + 16;        // [2], states after block kb: barrier kb % 2
     const uint32_t snapready = ready + 16;        // CTA 0: next pair's snapshots taken
     const uint32_t corr_bar = snapready + 8;      // staged coupling blocks of the own block
     const uint32_t gen_done = corr_bar + 8;       // CTA 0: CTA 1's generators finished pair P's main chunks
+    const uint32_t peer_full = gen_done + 8;      // CG2, CTA 0: [kNA] CTA 1's operands of the chunk in slot s
+    const uint32_t fin = peer_full + 8 * kNA;     // CG2: every MMA of the launch completed
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = (int)cluster_rank(), peer = r ^ 1;
     const int q = p.q, L = p.L, NC = p.NC, Lp = p.Lp;
@@ -397,26 +512,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             mbar_init(full_a + 8 * s, 1);
             mbar_init(empty_a + 8 * s, 1);
         }
-        for (int s = 0; s < kNB; ++s) {
+        for (int s = 0; s < NB; ++s) {
             mbar_init(full_b + 8 * s, kGenWarps);
             mbar_init(empty_b + 8 * s, 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full + 8 * s, 1);
-            mbar_init(acc_empty + 8 * s, kDrawWarps);
+            mbar_init(acc_empty + 8 * s, CG2 ? 2 * kDrawWarps : kDrawWarps);
             mbar_init(ready + 8 * s, kDraw);
         }
         mbar_init(snapready, kDraw);
         mbar_init(corr_bar, 1);
         mbar_init(gen_done, kGenWarps);
+        for (int s = 0; s < kNA; ++s) mbar_init(peer_full + 8 * s, 1);
+        mbar_init(fin, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(p.tmem_cols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (CG2) {  // one warp of each CTA of the pair; both get the same columns
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                         "r"(p.tmem_cols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                         "r"(p.tmem_cols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     for (int k = tid; k < NC * Lp; k += kThreads) {
         const int c = k / Lp, x = k - c * Lp;
@@ -425,8 +549,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     }
     for (int c = tid; c < p.nK; c += kThreads) {
         const int k0 = c * kKC;
-        jtab[2 * c] = (unsigned short)min(L - 1, k0 / q);
-        jtab[2 * c + 1] = (unsigned short)min(L - 1, (k0 + kKC - 1) / q);
+        jtab[4 * c] = (unsigned short)min(L - 1, k0 / q);
+        jtab[4 * c + 1] = (unsigned short)min(L - 1, (k0 + kKC / 2 - 1) / q);
+        jtab[4 * c + 2] = (unsigned short)min(L - 1, (k0 + kKC / 2) / q);
+        jtab[4 * c + 3] = (unsigned short)min(L - 1, (k0 + kKC - 1) / q);
     }
     __syncthreads();
     for (long long kb = 0; kb < 2 && kb < nblocks; ++kb) {  // snapshots of pair 0
@@ -462,7 +588,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (long long P = 0; P <= npairs && ok; ++P)
                 for (int step = 0; step < 4 && ok; ++step) {
-                    const Seg sg = seg_info(p, P, step, r);
+                    const Seg sg = CG2 ? seg_info_cg(p, P, step, r).s : seg_info(p, P, step, r);
                     const int r0 = sg.n > 0 ? (int)(sg.t % p.nb) * kRowsA : 0;
                     for (int k = 0; k < sg.n && ok; ++k) {
                         const int c = seg_chunk(sg, k);
@@ -484,6 +610,82 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 volatile int no_abort = 0;
                 for (long long u = issued > kNA ? issued - kNA : 0; u < issued; ++u)
                     mbar_wait(full_a + 8 * (int)(u % kNA), (uint32_t)((u / kNA) & 1), &no_abort, p.err);
+            }
+        }
+    } else if (warp == 1 && CG2) {
+        // ------------------------------------------------------------ paired MMA issuer (CTA 0)
+        if (lane == 0 && r == 0) {
+            // kind::f16: D F32 (bit 4), A = B = F16, K-major, N >> 3 at 17, M >> 4 at 24; M = 256
+            // across the pair (128 coupling rows per CTA), N = NC (NC/2 one-hot rows per CTA).
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)((2 * kRowsA) >> 4) << 24);
+            int sa = 0, sb = 0;
+            uint32_t pha = 0, phb = 0;
+            bool ok = true;
+            for (long long P = 0; P <= npairs && ok; ++P)
+                for (int step = 0; step < 4 && ok; ++step) {
+                    const SegCg gc = seg_info_cg(p, P, step, 0);
+                    const Seg &sg = gc.s;
+                    const long long j = gc.jd;
+                    for (int k = 0; k < sg.n && ok; ++k) {
+                        const int c = seg_chunk(sg, k);
+                        const bool first = !sg.delta && c == 0;
+                        if (!mbar_wait(full_b + 8 * sb, phb, abort_flag, p.err) ||
+                            !mbar_wait(full_a + 8 * sa, pha, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        // CTA 1's coupling tile and one-hot rows of this chunk (relayed by
+                        // its forwarding thread; slot sa of the coupling ring, same phase)
+                        if (!mbar_wait_cl(peer_full + 8 * sa, pha, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        if (first && j >= 2 &&
+                            !mbar_wait_cl(acc_empty + 8 * (int)(j & 1), (uint32_t)(((j - 2) >> 1) & 1), abort_flag,
+                                          p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t bb = su32(base + lay.b + sb * NCg * 128);
+                        const uint32_t ah = su32(base + lay.a + sa * kSlotA), al = ah + kTileA;
+                        const uint32_t dcol = tmem + (uint32_t)(j & 1) * p.acc_stride;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t bd = desc_noswz(bb + kk * 256);
+                            mma_f16_cg2(dcol, desc_sw128(ah + kk * 32), bd, idesc, (first && kk == 0) ? 0u : 1u);
+                            mma_f16_cg2(dcol, desc_sw128(al + kk * 32), bd, idesc, 1u);
+                        }
+                        // one commit per chunk frees both its coupling slot and its one-hot
+                        // slot (the generators wait on the coupling ring's barriers)
+                        mma_commit_mc(empty_a + 8 * sa, 3);
+                        if (++sa == kNA) {
+                            sa = 0;
+                            pha ^= 1u;
+                        }
+                        if (++sb == NB) {
+                            sb = 0;
+                            phb ^= 1u;
+                        }
+                    }
+                    if (ok && gc.commit_mask) mma_commit_mc(acc_full + 8 * (int)(j & 1), (uint16_t)gc.commit_mask);
+                }
+            mma_commit_mc(fin, 3);  // teardown waits for every MMA of the launch, in both CTAs
+        } else if (lane == 0) {
+            // CTA 1: relay, chunk by chunk, that this CTA's coupling tile and its
+            // one-hot rows are in place (one arrival on CTA 0's barrier of the
+            // chunk's coupling slot).  A slot's barrier cannot move on by two
+            // phases before CTA 0 has consumed the chunk: the chunk kNA later
+            // needs this slot refilled, which waits for that chunk's MMAs.
+            const uint32_t pf0 = peer_addr(peer_full, 0);
+            long long total = 0;
+            for (long long P = 0; P <= npairs; ++P)
+                for (int step = 0; step < 4; ++step) total += seg_info_cg(p, P, step, 1).s.n;
+            for (long long k = 0; k < total; ++k) {
+                if (!mbar_wait(full_a + 8 * (int)(k % kNA), (uint32_t)((k / kNA) & 1), abort_flag, p.err) ||
+                    !mbar_wait(full_b + 8 * (int)(k % NB), (uint32_t)((k / NB) & 1), abort_flag, p.err))
+                    break;
+                mbar_arrive_peer_relaxed(pf0 + 8 * (uint32_t)(k % kNA));
             }
         }
     } else if (warp == 1) {
@@ -525,13 +727,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                             mma_f16(dcol, desc_sw128(ah + kk * 32), bd, idesc, (first && kk == 0) ? 0u : 1u);
                             mma_f16(dcol, desc_sw128(al + kk * 32), bd, idesc, 1u);
                         }
-                        mma_commit(empty_a + 8 * sa);
+                        mma_commit(empty_a + 8 * sa);  // frees the chunk's coupling and one-hot slots
                         if (++sa == kNA) {
                             sa = 0;
                             pha ^= 1u;
                         }
-                        mma_commit(empty_b + 8 * sb);
-                        if (++sb == kNB) {
+                        if (++sb == NB) {
                             sb = 0;
                             phb ^= 1u;
                         }
@@ -585,13 +786,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 if (tm_reader && lane_base < r0 + q && lane_base + 32 > r0) {
                     const bool mine = row >= r0 && row < r0 + q;
                     const float hv = mine ? hrow[row] : 0.0f;
-                    for (int c0 = 0; c0 < NC; c0 += 16) {
-                        uint32_t v[16];
-                        tmem_ld16(tacc + (uint32_t)c0, v);
+                    // up to 48 columns (chains) in flight per wait: 16-column loads
+                    // issued back to back, then one wait (NC is a multiple of 16)
+                    for (int c0 = 0; c0 < NC; c0 += 48) {
+                        const int nc = min(48, NC - c0);
+                        uint32_t v[3][16];
+#pragma unroll
+                        for (int u = 0; u < 3; ++u)
+                            if (16 * u < nc) tmem_ld16(tacc + (uint32_t)(c0 + 16 * u), v[u]);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                         if (mine) {
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) Hs[(c0 + e) * HS + (row - r0)] = hv + __uint_as_float(v[e]);
+                            for (int u = 0; u < 3; ++u)
+                                if (16 * u < nc) {
+#pragma unroll
+                                    for (int e = 0; e < 16; ++e)
+                                        Hs[(c0 + 16 * u + e) * HS + (row - r0)] = hv + __uint_as_float(v[u][e]);
+                                }
                         }
                     }
                 }
@@ -634,7 +845,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty + 8 * slot);
+            if (lane == 0) {
+                if (CG2 && r == 1)
+                    mbar_arrive_peer(peer_addr(acc_empty + 8 * (uint32_t)slot, 0));
+                else
+                    mbar_arrive(acc_empty + 8 * slot);
+            }
             named_bar_sync(1, kDraw);  // the staged coupling blocks are free again
             if (w == 0 && ok && !*abort_flag && kb + 2 < nblocks) {
                 stage_corr(kb + 2);
@@ -684,13 +900,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------------------ generators (warps 7-11)
-        const int w = tid - 64 - kDraw;  // 0..kGen-1, operand row of chain w
-        const bool own = w < NC;
+        // One thread per operand row; with paired tensor cores (NC/2 rows per
+        // CTA) two threads per row, each writing one 32-column half of a chunk.
+        // kNS bounds the sites a thread's columns touch for alphabets of this
+        // QC (q > QC - 8): chunks within it take the unrolled path.
+        constexpr int kNS = QC == 8 ? 8 : (CG2 ? 32 : 64) / (QC - 7) + 2 > 8 ? 8 : (CG2 ? 32 : 64) / (QC - 7) + 2;
+        const int gt = tid - 64 - kDraw;             // 0..kGen-1
+        const int w = CG2 ? gt >> 1 : gt;            // operand row of this CTA
+        const int cb = CG2 ? 32 * (gt & 1) : 0;      // chunk columns [cb, ce) of this thread
+        const int ce = CG2 ? cb + 32 : kKC;
+        const bool own = w < NCg;
+        const int ch = (CG2 ? r * NCg : 0) + (own ? w : 0);  // its chain
         unsigned char *const row0 = base + lay.b + noswz_off(own ? w : 0, 0);
-        const uint8_t *const strow = st + (own ? w : 0) * Sst;
-        const int wrow = (own ? w : 0) * Ssn;
+        const uint8_t *const strow = st + ch * Sst;
+        const int wrow = ch * Ssn;
         const uint32_t gen_done_peer = peer_addr(gen_done, (uint32_t)peer);
         int sb = 0, lap = 0;
+        long long gk = 0;  // chunks generated so far
         bool ok = true;
         for (long long P = 0; P <= npairs && ok; ++P) {
             int s0lo = L, s0hi = L, s1lo = L, s1hi = L;
@@ -705,7 +931,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 ps1 = snap_of(2 * P - 1) + wrow;
             }
             for (int step = 0; step < 4 && ok; ++step) {
-                const Seg sg = seg_info(p, P, step, r);
+                const Seg sg = CG2 ? seg_info_cg(p, P, step, r).s : seg_info(p, P, step, r);
                 if (sg.n > 0 && sg.wait_kind != 0) {
                     const uint32_t bar = sg.wait_kind == 1 ? ready + 8 * (uint32_t)(sg.wait_kb & 1) : snapready;
                     if (!mbar_wait_cl(bar, (uint32_t)((sg.wait_kb >> 1) & 1), abort_flag, p.err)) {
@@ -713,40 +939,68 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         break;
                     }
                 }
-                for (int k = 0; k < sg.n; ++k) {
-                    const int c = seg_chunk(sg, k);
-                    const int k0 = c * kKC;
-                    // Main chunks touching at most 8 sites (q >= 8): the positions of
-                    // the row's nonzeros are found before the slot wait, with
-                    // independent loads, so only the stores remain after it.
-                    const int jlo = jtab[2 * c], jhi = jtab[2 * c + 1];
-                    const bool fast = !sg.delta && jhi - jlo < 8;
-                    int fpos[8];
+                // Main chunks touching at most 8 sites (q >= 8): the state bytes of
+                // the row's nonzeros are loaded one chunk ahead (before the previous
+                // chunk's slot wait and stores), so their latency is hidden and only
+                // the stores remain after the wait.
+                auto chunk_sites = [&](int kk, int &jlo, int &jhi, bool &fast) {
+                    const int c = seg_chunk(sg, kk);
+                    jlo = jtab[4 * c + (CG2 ? 2 * (cb >> 5) : 0)];
+                    jhi = jtab[4 * c + (CG2 ? 2 * (cb >> 5) + 1 : 3)];
+                    fast = !sg.delta && jhi - jlo < kNS;
+                };
+                auto load_states = [&](int jlo, int jhi, bool fast, int (&sv)[kNS]) {
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) {
+                    for (int t = 0; t < kNS; ++t) {
                         const int jj = jlo + t;
-                        fpos[t] = -1;
+                        sv[t] = -1;
                         if (fast && own && jj <= jhi) {
                             const uint8_t *src = strow + jj;
                             src = (jj >= s0lo && jj < s0hi) ? ps0 + (jj - s0lo) : src;
                             src = (jj >= s1lo && jj < s1hi) ? ps1 + (jj - s1lo) : src;
-                            fpos[t] = jj * q + *src - k0;
+                            sv[t] = *src;
                         }
                     }
-                    if (lap > 0 && !mbar_wait(empty_b + 8 * sb, (uint32_t)((lap - 1) & 1), abort_flag, p.err)) {
+                };
+                int nxt_lo = 0, nxt_hi = 0, nxt_sv[kNS];
+                bool nxt_fast = false;
+                if (sg.n > 0) {
+                    chunk_sites(0, nxt_lo, nxt_hi, nxt_fast);
+                    load_states(nxt_lo, nxt_hi, nxt_fast, nxt_sv);
+                }
+                for (int k = 0; k < sg.n; ++k) {
+                    const int c = seg_chunk(sg, k);
+                    const int k0 = c * kKC;
+                    const int jlo = nxt_lo, jhi = nxt_hi;
+                    const bool fast = nxt_fast;
+                    int fpos[kNS];
+#pragma unroll
+                    for (int t = 0; t < kNS; ++t) fpos[t] = nxt_sv[t] >= 0 ? (jlo + t) * q + nxt_sv[t] - k0 : -1;
+                    if (k + 1 < sg.n) {
+                        chunk_sites(k + 1, nxt_lo, nxt_hi, nxt_fast);
+                        load_states(nxt_lo, nxt_hi, nxt_fast, nxt_sv);
+                    }
+                    // one-hot slot sb is free once the MMAs of chunk gk - NB completed:
+                    // the commit of that chunk on the coupling ring's barrier.  NB <= kNA,
+                    // so that barrier cannot have moved on by a further phase (that
+                    // chunk's successor there needs a one-hot tile not yet written).
+                    if (gk >= NB && !mbar_wait(empty_a + 8 * (int)((gk - NB) % kNA),
+                                               (uint32_t)(((gk - NB) / kNA) & 1), abort_flag, p.err)) {
                         ok = false;
                         break;
                     }
-                    unsigned char *rowp = row0 + sb * NC * 128;
+                    ++gk;
+                    unsigned char *rowp = row0 + sb * NCg * 128;
                     if (own) {
 #pragma unroll
                         for (int pc = 0; pc < 8; ++pc)
-                            *reinterpret_cast<uint4 *>(rowp + pc * 128) = make_uint4(0, 0, 0, 0);
+                            if (pc * 8 >= cb && pc * 8 < ce)
+                                *reinterpret_cast<uint4 *>(rowp + pc * 128) = make_uint4(0, 0, 0, 0);
                         if (fast) {
 #pragma unroll
-                            for (int t = 0; t < 8; ++t) {
+                            for (int t = 0; t < kNS; ++t) {
                                 const int pos = fpos[t];
-                                if (pos >= 0 && pos < kKC)
+                                if (pos >= cb && pos < ce)
                                     *reinterpret_cast<unsigned short *>(rowp + (pos >> 3) * 128 + (pos & 7) * 2) =
                                         0x3c00u;
                             }
@@ -756,7 +1010,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                                                : (jj >= s1lo && jj < s1hi) ? ps1[jj - s1lo]
                                                                            : strow[jj];
                                 const int pos = jj * q + sj - k0;
-                                if (pos >= 0 && pos < kKC)
+                                if (pos >= cb && pos < ce)
                                     *reinterpret_cast<unsigned short *>(rowp + (pos >> 3) * 128 + (pos & 7) * 2) =
                                         0x3c00u;
                             }
@@ -771,10 +1025,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                                     const int sn = strow[jj], so = po[x];
                                     if (sn == so) continue;
                                     const int pn = jj * q + sn - k0, pd = jj * q + so - k0;
-                                    if (pn >= 0 && pn < kKC)
+                                    if (pn >= cb && pn < ce)
                                         *reinterpret_cast<unsigned short *>(rowp + (pn >> 3) * 128 + (pn & 7) * 2) =
                                             0x3c00u;
-                                    if (pd >= 0 && pd < kKC)
+                                    if (pd >= cb && pd < ce)
                                         *reinterpret_cast<unsigned short *>(rowp + (pd >> 3) * 128 + (pd & 7) * 2) =
                                             0xbc00u;
                                 }
@@ -784,7 +1038,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(full_b + 8 * sb);
-                    if (++sb == kNB) {
+                    if (++sb == NB) {
                         sb = 0;
                         ++lap;
                     }
@@ -799,12 +1053,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
         if (!ok) *abort_flag = 1;
     }
+    if (CG2 && warp == 1 && lane == 0) {  // CTA 0's MMAs write both CTAs' tensor memory
+        volatile int no_abort = 0;
+        mbar_wait(fin, 0, &no_abort, p.err);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 1)
+    if (CG2) {
+        cluster_sync_all();
+        if (warp == 1)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols)
+                         : "memory");
+    } else if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols)
                      : "memory");
+    }
     // No remote store or arrival into either CTA is in flight past this
     // barrier; then each CTA reads the other's abort flag, and the second
     // barrier keeps both CTAs resident until those reads are done.
@@ -1433,14 +1697,14 @@ int max_clusters(const bm_model_s *m)
     std::call_once(g_clusters_once[dev], [&] {
         int n = (m->num_sms > 0 ? m->num_sms : 2) / 2;
         const int smem = 200 * 1024;  // any size above half an SM's shared memory: one CTA per SM
-        if (cudaFuncSetAttribute(k_gibbs_pair<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+        if (cudaFuncSetAttribute(k_gibbs_pair<false, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
             cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(2, 1, 1);
             cfg.blockDim = dim3(kThreads, 1, 1);
             cfg.dynamicSmemBytes = smem;
             int c = 0;  // the kernel's cluster shape (2 CTAs) is fixed at compile time
-            if (cudaOccupancyMaxActiveClusters(&c, k_gibbs_pair<false, 32>, &cfg) == cudaSuccess && c > 0) n = c;
+            if (cudaOccupancyMaxActiveClusters(&c, k_gibbs_pair<false, 32, false>, &cfg) == cudaSuccess && c > 0) n = c;
         }
         (void)cudaGetLastError();
         g_max_clusters[dev] = n > 0 ? n : 1;
@@ -1450,7 +1714,7 @@ int max_clusters(const bm_model_s *m)
 
 // Largest chains per cluster (multiple of 16, <= min(cap, 160)) whose layout
 // fits one CTA's shared memory; 0 when none does or the shape is unsupported.
-int fit_nc(const bm_model_s *m, int cap)
+int fit_nc(const bm_model_s *m, int cap, bool cg2 = false)
 {
     if (m->L < 2 || m->L > 65535 || m->q > kQmax) return 0;
     const int B = bm_split_block_sites(m->L, m->q);
@@ -1458,14 +1722,16 @@ int fit_nc(const bm_model_s *m, int cap)
     const int Lp = (m->L + 15) & ~15;
     const int nK = (m->L * m->q + kKC - 1) / kKC;
     int nc = std::min(cap, kNCmax) & ~15;
-    while (nc >= 16 && smem_layout(nc, Lp, B, nK, m->q).total + 1024 > 227 * 1024) nc -= 16;
+    while (nc >= 16 && smem_layout(nc, Lp, B, nK, m->q, cg2 ? nc / 2 : nc).total + 1024 > 227 * 1024) nc -= 16;
     return nc >= 16 ? nc : 0;
 }
 
-size_t smem_bytes(const bm_model_s *m, int nc)
+size_t smem_bytes(const bm_model_s *m, int nc, bool cg2 = false)
 {
     const int B = bm_split_block_sites(m->L, m->q);
-    return (size_t)smem_layout(nc, (m->L + 15) & ~15, B, (m->L * m->q + kKC - 1) / kKC, m->q).total + 1024;
+    return (size_t)smem_layout(nc, (m->L + 15) & ~15, B, (m->L * m->q + kKC - 1) / kKC, m->q, cg2 ? nc / 2 : nc)
+               .total +
+           1024;
 }
 
 void fill_args(const bm_model_s *m, const bm_chains_s *c, int NC, int nsweeps, float beta, uint8_t *states,
@@ -1495,22 +1761,22 @@ void fill_args(const bm_model_s *m, const bm_chains_s *c, int NC, int nsweeps, f
     a.nmma = 0;
 }
 
-// The shared-memory operand kernel for q rounded up to 8.
-template <bool BATCH>
+// The shared-memory operand kernel for q rounded up to 8 (CG2: paired tensor cores).
+template <bool BATCH, bool CG2 = false>
 int launch_smem(int q, int grid, size_t smem, cudaStream_t st, const CUtensorMap &tm, const PairArgs &a,
                 const PairItem *items)
 {
     auto go = [&](auto kern) -> int {
         BM_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<grid, kThreads, smem, st>>>(tm, a, items);
-        BM_CK_LAUNCH(BATCH ? "k_gibbs_pair (batch)" : "k_gibbs_pair");
+        BM_CK_LAUNCH(BATCH ? "k_gibbs_pair (batch)" : CG2 ? "k_gibbs_pair (paired tensor cores)" : "k_gibbs_pair");
         return BM_OK;
     };
     switch ((q + 7) / 8) {
-    case 1: return go(k_gibbs_pair<BATCH, 8>);
-    case 2: return go(k_gibbs_pair<BATCH, 16>);
-    case 3: return go(k_gibbs_pair<BATCH, 24>);
-    default: return go(k_gibbs_pair<BATCH, 32>);
+    case 1: return go(k_gibbs_pair<BATCH, 8, CG2>);
+    case 2: return go(k_gibbs_pair<BATCH, 16, CG2>);
+    case 3: return go(k_gibbs_pair<BATCH, 24, CG2>);
+    default: return go(k_gibbs_pair<BATCH, 32, CG2>);
     }
 }
 
@@ -1610,6 +1876,29 @@ int bm_gibbs_pair_waves(const bm_model_s *m, int M)
     if (nc == 0) return 0;
     const int ncl = max_clusters(m);
     return ((M + nc - 1) / nc + ncl - 1) / ncl;
+}
+
+// Chains per cluster of the paired-tensor-core form (multiple of 16, <= 160),
+// 0 when it does not fit.
+int bm_gibbs_paired_chains_per_cluster(const bm_model_s *m, int M)
+{
+    const int ncl = max_clusters(m);
+    const int want = std::max(16, (((M + ncl - 1) / ncl) + 15) & ~15);
+    return fit_nc(m, want, true);
+}
+
+int bm_launch_gibbs_paired(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)
+{
+    const int NC = bm_gibbs_paired_chains_per_cluster(m, c->M);
+    if (NC == 0) return bm_fail(BM_EINVAL, "paired tensor-core sweep: shape does not fit shared memory");
+    const int rc = model_prepare(m, st);
+    if (rc != BM_OK) return rc;
+    PairArgs a;
+    fill_args(m, c, NC, nsweeps, beta, c->s, a);
+    const size_t smem = smem_bytes(m, NC, true);
+    const int nclusters = (c->M + NC - 1) / NC;
+    return launch_smem<false, true>(a.q, 2 * nclusters, smem, st, *reinterpret_cast<const CUtensorMap *>(m->tmap_jp),
+                                    a, nullptr);
 }
 
 int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)

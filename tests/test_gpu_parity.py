@@ -29,14 +29,15 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-GIBBS_ENGINES = ["simt", "mma", "mma_pair"]
+GIBBS_ENGINES = ["simt", "mma", "mma_pair", "mma_pair2"]
 
 
 def load(bm, h, J, engine=None):
     m = bm.bm_potts_load(to_dev(h), to_dev(J))
     if engine is not None:
         bm.bm_model_set_engine(m, {"simt": bm.BM_ENGINE_SIMT, "mma": bm.BM_ENGINE_MMA,
-                                   "mma_pair": bm.BM_ENGINE_MMA_PAIR}[engine])
+                                   "mma_pair": bm.BM_ENGINE_MMA_PAIR,
+                                   "mma_pair2": bm.BM_ENGINE_MMA_PAIR2}[engine])
     return m
 
 
