@@ -51,7 +51,7 @@ UNIT = "site-updates/s"
 # DRAM bytes per 10-sweep launch of each sweep kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of this bench's launch); None
 # whenever the kernel has changed since it was captured.
-TRAFFIC_GIBBS = {"k_gibbs_pair": 1192470272 + 3264256}
+TRAFFIC_GIBBS = {}
 
 
 def parse():
@@ -265,6 +265,7 @@ def split_precision_leg(bmdca, synth, timed):
         out[f"site_updates_per_s_{name}"] = M * L / (ms * 1e-3)
         form = bmdca.bm_model_sweep_engine(model, M)
         out[f"engine_{name}"] = {bmdca.BM_ENGINE_MMA_PAIR: "two-CTA tensor cores (fp16 hi+lo)",
+                                 bmdca.BM_ENGINE_MMA_PAIR2: "paired two-CTA tensor cores (fp16 hi+lo)",
                                  bmdca.BM_ENGINE_MMA: "one-CTA tensor cores (fp16 hi+lo)"}.get(
                                      form, "CUDA-core FP32 gather")
         c.free()
@@ -483,7 +484,8 @@ def run_ours(args, rank, world, local):
     achieved = flops_per_launch / (ms_gibbs * 1e-3) / 1e12
     bmdca.bm_model_set_engine(model, bmdca.BM_ENGINE_AUTO)
     form = bmdca.bm_model_sweep_engine(model, M_CHAINS)
-    kname = {bmdca.BM_ENGINE_MMA_PAIR: "k_gibbs_pair", bmdca.BM_ENGINE_MMA: "k_gibbs_mma"}.get(form, "k_gibbs_staged")
+    kname = {bmdca.BM_ENGINE_MMA_PAIR: "k_gibbs_pair", bmdca.BM_ENGINE_MMA_PAIR2: "k_gibbs_pair (paired tensor cores)",
+             bmdca.BM_ENGINE_MMA: "k_gibbs_mma"}.get(form, "k_gibbs_staged")
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved / peak_tf, "traffic": TRAFFIC_GIBBS.get(kname),
                 "kernel": kname,

@@ -362,21 +362,16 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
 }  // extern "C"
 
 // AUTO: do the tensor-core forms beat the CUDA-core gather for this shape?
-// Measured on an L x q x M grid (L 48-256, q 4-21, M 1000-20000): the
+// Measured on an L x q x M grid (L 48-400, q 4-21, M 1000-20000): the
 // tensor-core forms redraw the sites of a block one after another, which
-// puts a floor of a few microseconds per site under a sweep, so small
-// problems (short L, few chains) go to the gather; the gather's efficiency
-// also depends on q (alphabets of 5-7 symbols suit its lane layout best).
-// Rule: tensor cores when M*L^2 >= T(q) and L >= L0(q).
+// puts a floor of a few microseconds per site under a sweep, so short
+// sequences with few chains go to the gather.  Rule: tensor cores from
+// L = 120 (and M >= 512), and for alphabets of 10 or more symbols also from
+// L = 48 once M * L >= 3e5.
 static bool tensor_beats_gather(int L, int q, int M)
 {
-    const double work = (double)M * L * L;
-    if (q >= 16) return work >= 2e7 && L >= 48;
-    if (q >= 10) return work >= 5e7 && L >= 100;
-    if (q >= 8) return work >= 2.5e8 && L >= 120;
-    if (q >= 5) return work >= 5e8 && L >= 180;
-    if (q >= 2) return work >= 5e7 && L >= 150;
-    return false;
+    if (L >= 120) return M >= 512;
+    return q >= 10 && L >= 48 && (double)M * L >= 3e5;
 }
 
 int bm_sweep_form(const bm_model_s *m, int M)
@@ -385,29 +380,24 @@ int bm_sweep_form(const bm_model_s *m, int M)
     if (m->engine == BM_ENGINE_MMA_PAIR) return 2;
     if (m->engine == BM_ENGINE_MMA) return 1;
     if (m->engine != BM_ENGINE_AUTO) return 0;
-    // Alphabets of 4-8 symbols with blocks whose K chunks are at most three
-    // times their sites: the two-CTA sweep in its tensor-memory operand form
-    // (measured 1.1-2.0x ahead of the other forms at L 120-500, M 4096-20000;
-    // behind for q = 2, for q = 21 at short L and near 4 chunks per site).
-    if (M >= 4096 && m->L >= 120 && m->q >= 4 && m->q <= 8 && bm_gibbs_pair_tm(m) &&
-        (m->L * m->q + 63) / 64 <= 3 * bm_split_block_sites(m->L, m->q))
-        return 2;
     if (!tensor_beats_gather(m->L, m->q, M)) return 0;
-    // the two-CTA form (half the coupling bytes per SM) when it needs no more
-    // waves of CTAs than the one-CTA form and the block pairs are long enough
-    // for the MMAs, not the two redraws per pair, to set the pace: the MMA
-    // work of a pair grows as L*q^2 against the redraws, and redraws are
-    // slower with many chains per cluster (measured at q = 21: two-CTA ahead
-    // from L = 240 at 144 chains per cluster, from L = 160 at <= 32).
-    const int nc1 = bm_gibbs_mma_chains_per_cta(m, M);
-    const int w2 = bm_gibbs_pair_waves(m, M);
-    if (nc1 == 0) return w2 > 0 ? 2 : 0;
-    if (w2 == 0) return 1;
-    const int nsm = m->num_sms > 0 ? m->num_sms : 1;
-    const int w1 = ((M + nc1 - 1) / nc1 + nsm - 1) / nsm;
-    const long long lq2 = (long long)m->L * m->q * m->q;
-    const long long need = bm_gibbs_pair_chains_per_cluster(m, M) > 96 ? 98000 : 63000;
-    return (w2 <= w1 && lq2 >= need) ? 2 : 1;
+    // Among the tensor-core forms (same grid; the one-CTA form was never the
+    // fastest): the two-CTA engine (form 2) and the paired-tensor-core form
+    // (form 3) trade places with the cluster count.
+    const int w3 = bm_gibbs_paired_waves(m, M), w2 = bm_gibbs_pair_waves(m, M);
+    if (w3 == 0) return w2 > 0 ? 2 : (bm_gibbs_mma_chains_per_cta(m, M) > 0 ? 1 : 0);
+    if (w2 == 0) return 3;
+    if (bm_gibbs_pair_tm(m)) {
+        // form 2 runs its tensor-memory operand form here, 128 chains per
+        // cluster: the paired form wins where it fits one wave and form 2
+        // does not, or where it spreads the chains at most 32 per cluster
+        if (w3 == 1 && w2 > 1) return 3;
+        return bm_gibbs_paired_chains_per_cluster(m, M) <= 32 ? 3 : 2;
+    }
+    // both with shared-memory operands: halving each SM's one-hot work pays
+    // while the pair's MMAs are short (L q^2 below ~90,000: q = 21 up to
+    // L ~ 200, q = 12 up to L ~ 600)
+    return (long long)m->L * m->q * m->q < 90000 ? 3 : 2;
 }
 
 int bm_sweep_run(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)

@@ -152,6 +152,7 @@ int bm_pair_batch_autotune(bm_pair_batch_s *b, cudaStream_t st);
 void bm_pair_batch_shape(const bm_pair_batch_s *b, int *nc, int *ctas);
 int bm_launch_gibbs_pair(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
 int bm_gibbs_paired_chains_per_cluster(const bm_model_s *m, int M);
+int bm_gibbs_paired_waves(const bm_model_s *m, int M);
 int bm_launch_gibbs_paired(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st);
 // Tensor-core sweep form for this model and chain count: 2 = two-CTA
 // clusters, 1 = one CTA, 0 = CUDA cores (the model's engine, AUTO resolved).

@@ -1020,7 +1020,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                                 if (db < 0) continue;
                                 const Blk gd = blk_of(p, db);
                                 const uint8_t *po = (u == 0 ? ps0 : ps1);  // d0 = 2P-2, d1 = 2P-1
-                                for (int x = 0; x < gd.Bk; ++x) {
+                                // only the block's sites inside this thread's columns
+                                const int x0 = max(0, jlo - gd.i0), x1 = min(gd.Bk, jhi - gd.i0 + 1);
+                                for (int x = x0; x < x1; ++x) {
                                     const int jj = gd.i0 + x;
                                     const int sn = strow[jj], so = po[x];
                                     if (sn == so) continue;
@@ -1885,6 +1887,15 @@ int bm_gibbs_paired_chains_per_cluster(const bm_model_s *m, int M)
     const int ncl = max_clusters(m);
     const int want = std::max(16, (((M + ncl - 1) / ncl) + 15) & ~15);
     return fit_nc(m, want, true);
+}
+
+// Waves of clusters the paired-tensor-core sweep of M chains needs (0: does not fit).
+int bm_gibbs_paired_waves(const bm_model_s *m, int M)
+{
+    const int nc = bm_gibbs_paired_chains_per_cluster(m, M);
+    if (nc == 0) return 0;
+    const int ncl = max_clusters(m);
+    return ((M + nc - 1) / nc + ncl - 1) / ncl;
 }
 
 int bm_launch_gibbs_paired(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)

@@ -660,9 +660,13 @@ def test_shards_reproduce_the_full_ensemble(bm, engine):
 
 
 def test_sweep_engine_resolution(bm):
-    """AUTO: CUDA cores for small problems, the tensor cores for large ones
-    (thresholds by alphabet size), and among those the two-CTA form for long
-    block pairs, the one-CTA form for short ones; explicit engines are kept."""
+    """AUTO (rules fitted to a measured L x q x M grid): CUDA cores for short
+    sequences with few chains, tensor cores otherwise; among those the
+    paired-tensor-core form for short coupling rows (L q^2 < 90000) and the
+    two-CTA form for long ones; for small alphabets the two-CTA form runs
+    its tensor-memory operand form unless that needs more waves of clusters
+    than the paired form fitting one wave, or the paired form spreads the
+    chains at most 32 per cluster.  Explicit engines are kept."""
     h, J = synth.planted_local_model(256, 21, 3)
     m = load(bm, h, J)
     assert bm.bm_model_sweep_engine(m, 10000) == bm.BM_ENGINE_MMA_PAIR
@@ -671,32 +675,32 @@ def test_sweep_engine_resolution(bm):
     bm.bm_model_set_engine(m, bm.BM_ENGINE_MMA)
     assert bm.bm_model_sweep_engine(m, 1) == bm.BM_ENGINE_MMA
     assert bm.bm_model_sweep_engine(m, 10000) == bm.BM_ENGINE_MMA
-    # short block pairs: the two redraws per pair set the pace, one CTA is faster
+    bm.bm_model_set_engine(m, bm.BM_ENGINE_MMA_PAIR2)
+    assert bm.bm_model_sweep_engine(m, 10000) == bm.BM_ENGINE_MMA_PAIR2
+    # short coupling rows: the paired tensor cores
     hs, Js = synth.planted_local_model(120, 21, 3)
     ms = load(bm, hs, Js)
-    assert bm.bm_model_sweep_engine(ms, 10000) == bm.BM_ENGINE_MMA
-    assert bm.bm_model_sweep_engine(ms, 1024) == bm.BM_ENGINE_SIMT  # M*L^2 below 2e7 at q = 21
+    assert bm.bm_model_sweep_engine(ms, 10000) == bm.BM_ENGINE_MMA_PAIR2
+    assert bm.bm_model_sweep_engine(ms, 1024) == bm.BM_ENGINE_MMA_PAIR2
     hm, Jm = synth.planted_local_model(200, 21, 3)
     mm = load(bm, hm, Jm)
-    assert bm.bm_model_sweep_engine(mm, 10000) == bm.BM_ENGINE_MMA
-    assert bm.bm_model_sweep_engine(mm, 1024) == bm.BM_ENGINE_MMA_PAIR
+    assert bm.bm_model_sweep_engine(mm, 10000) == bm.BM_ENGINE_MMA_PAIR2
     h5, J5 = synth.planted_local_model(64, 5, 3)
     m5 = load(bm, h5, J5)
     assert bm.bm_model_sweep_engine(m5, 10000) == bm.BM_ENGINE_SIMT
-    # small problems go to the gather; large small-alphabet ones to the tensor cores
+    # short sequences with few chains go to the gather even for large alphabets
     h48, J48 = synth.planted_local_model(48, 21, 3)
-    assert bm.bm_model_sweep_engine(load(bm, h48, J48), 1000) == bm.BM_ENGINE_SIMT
-    # alphabets of 4-8 symbols with many sites per block: the two-CTA sweep
-    # (tensor-memory operand form) from L = 120 and M = 4096
+    m48 = load(bm, h48, J48)
+    assert bm.bm_model_sweep_engine(m48, 1000) == bm.BM_ENGINE_SIMT
+    assert bm.bm_model_sweep_engine(m48, 10000) == bm.BM_ENGINE_MMA_PAIR2
+    # small alphabets: the two-CTA form's tensor-memory operand form while it
+    # fits one wave with more than 32 chains per paired cluster
     h4, J4 = synth.planted_local_model(256, 4, 3)
     m4 = load(bm, h4, J4)
     assert bm.bm_model_sweep_engine(m4, 5000) == bm.BM_ENGINE_MMA_PAIR
+    assert bm.bm_model_sweep_engine(m4, 10000) == bm.BM_ENGINE_MMA_PAIR2  # 79 clusters of 128: two waves
+    assert bm.bm_model_sweep_engine(m4, 1000) == bm.BM_ENGINE_MMA_PAIR2
     assert bm.bm_model_sweep_engine(m4, 500) == bm.BM_ENGINE_SIMT
-    h6, J6 = synth.planted_local_model(256, 5, 3)
-    m6 = load(bm, h6, J6)
-    assert bm.bm_model_sweep_engine(m6, 20000) == bm.BM_ENGINE_MMA_PAIR
-    assert bm.bm_model_sweep_engine(m6, 5000) == bm.BM_ENGINE_MMA_PAIR
-    assert bm.bm_model_sweep_engine(m6, 2000) == bm.BM_ENGINE_SIMT
     with pytest.raises(bm.BmError) as e:
         bm.bm_model_sweep_engine(m5, 0)
     assert e.value.code == bm.BM_EINVAL
