@@ -15,6 +15,8 @@ in the C file; in short:
   energy .................. Eq. 1
   fields / conditional .... Eq. 1 with all but one site fixed
   gibbs / gibbs_verify .... Sec. 2.1 (PCD Gibbs sweeps), Sec. 3.3 (sweep)
+  metropolis / _flips ..... Sec. 2.1 (Metropolis-Hastings sweeps, the
+                            --sampler option)
   chain_stats ............. Sec. 2.1 (p_i, p_ij from the chains)
   seq_weights ............. Eq. 7 (80% identity weights), M_eff Sec. 3.3
   data_stats .............. Eq. 3 + pseudocount Eqs. 8-9
@@ -71,6 +73,9 @@ def _load():
         "orc_gibbs_verify": (ctypes.c_long, [P, P, I, I, I, P, P, U64, U64, U64, D, P, P]),
         "orc_gibbs_verify_rec": (ctypes.c_long, [P, P, I, I, I, P, P, U64, U64, U64, D, P, P,
                                                  ctypes.c_long, P, P, P, P, P]),
+        "orc_metropolis": (None, [P, P, I, I, I, P, U64, U64, U64, I, D]),
+        "orc_metropolis_verify_rec": (ctypes.c_long, [P, P, I, I, I, P, P, U64, U64, U64, D, P, P,
+                                                      ctypes.c_long, P, P, P, P, P]),
         "orc_chain_stats": (None, [P, I, I, I, P]),
         "orc_seq_weights": (None, [P, I, I, I, P, P]),
         "orc_data_stats": (None, [P, P, I, I, I, D, P, P]),
@@ -204,6 +209,37 @@ def gibbs_flips(h, J, before, after, seed: int, sweep: int, beta: float = 1.0, c
     rw = np.zeros(cap, dtype=np.int32)
     bad = _load().orc_gibbs_verify_rec(_p(h), _p(J), L, q, M, _p(b), _p(a), seed, chain0, sweep, beta,
                                        _p(mx), _p(mn), cap, _p(rc), _p(rs), _p(rm), _p(rg), _p(rw))
+    flips = [{"chain": int(rc[k]) + chain0, "site": int(rs[k]), "margin": float(rm[k]),
+              "got": int(rg[k]), "want": int(rw[k])} for k in range(min(int(bad), cap))]
+    return int(bad), float(mn[0]), flips
+
+
+def metropolis(h, J, states, seed: int, sweep0: int, nsweeps: int, beta: float = 1.0,
+               chain0: int = 0) -> np.ndarray:
+    """Run nsweeps sequential Metropolis-Hastings sweeps on a copy of states."""
+    h, J, L, q = _shape_hJ(h, J)
+    S = np.array(states, dtype=np.uint8, copy=True, order="C")
+    _load().orc_metropolis(_p(h), _p(J), L, q, S.shape[0], _p(S), seed, chain0, sweep0, nsweeps, beta)
+    return S
+
+
+def metropolis_flips(h, J, before, after, seed: int, sweep: int, beta: float = 1.0, chain0: int = 0,
+                     cap: int = 4096):
+    """Teacher-forced check of one Metropolis sweep: (n_bad, min_margin, flips)
+    with the flips recorded as in gibbs_flips."""
+    h, J, L, q = _shape_hJ(h, J)
+    b = _u8(before)
+    a = _u8(after)
+    M = b.shape[0]
+    mx = np.zeros(1)
+    mn = np.zeros(1)
+    rc = np.zeros(cap, dtype=np.int64)
+    rs = np.zeros(cap, dtype=np.int32)
+    rm = np.zeros(cap, dtype=np.float64)
+    rg = np.zeros(cap, dtype=np.int32)
+    rw = np.zeros(cap, dtype=np.int32)
+    bad = _load().orc_metropolis_verify_rec(_p(h), _p(J), L, q, M, _p(b), _p(a), seed, chain0, sweep, beta,
+                                            _p(mx), _p(mn), cap, _p(rc), _p(rs), _p(rm), _p(rg), _p(rw))
     flips = [{"chain": int(rc[k]) + chain0, "site": int(rs[k]), "margin": float(rm[k]),
               "got": int(rg[k]), "want": int(rw[k])} for k in range(min(int(bad), cap))]
     return int(bad), float(mn[0]), flips

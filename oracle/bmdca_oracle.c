@@ -255,6 +255,93 @@ long orc_gibbs_verify(const double *h, const double *J, int L, int q, int M,
 }
 
 /* ------------------------------------------------------------------------
+ * Metropolis-Hastings sweeps (Sec. 2.1: chains are updated "using Gibbs or
+ * Metropolis-Hastings sampling steps"; the --sampler option of the
+ * training and sampling commands).  The paper states no proposal; the
+ * readings taken here:
+ *   - sites visited in order 0..L-1, one proposal per site per sweep;
+ *   - proposal a' uniform over the q-1 symbols other than the current s_i
+ *     (symmetric, so the Hastings ratio is the Boltzmann ratio):
+ *     k = floor(u24_p (q-1) / 2^24) from Philox tag 2, a' = k + (k >= s_i);
+ *   - acceptance with probability min(1, exp(beta (H_i(a') - H_i(s_i)))),
+ *     H_i(a) = h_i(a) + sum_{j != i} J_ij(a, s_j): accepted iff
+ *     u_a < exp(beta dH), u_a = u24_a / 2^24 from Philox tag 3 (dH >= 0 is
+ *     always accepted since u_a < 1);
+ *   - q = 1: nothing to propose, the state is kept.
+ * The margin of a decision is |u_a - min(1, exp(beta dH))|.
+ * ---------------------------------------------------------------------- */
+static int orc_metropolis_step(const double *h, const double *J, int L, int q, const uint8_t *s, int i,
+                               double beta, uint64_t seed, uint64_t chain, uint64_t sweep, double *margin)
+{
+    if (q < 2) {
+        if (margin) *margin = INFINITY;
+        return s[i];
+    }
+    double H[64];
+    orc_fields(h, J, L, q, s, i, H);
+    const uint32_t rp = orc_u24(seed, chain, sweep, (uint64_t)i, 2);
+    const uint32_t ra = orc_u24(seed, chain, sweep, (uint64_t)i, 3);
+    int prop = (int)(((uint64_t)rp * (uint64_t)(q - 1)) >> 24);
+    if (prop >= s[i]) prop += 1;
+    const double dH = H[prop] - H[s[i]];
+    const double pacc = dH >= 0.0 ? 1.0 : exp(beta * dH);
+    const double u = (double)ra * (1.0 / 16777216.0);
+    if (margin) *margin = fabs(u - pacc);
+    return u < pacc ? prop : s[i];
+}
+
+void orc_metropolis(const double *h, const double *J, int L, int q, int M, uint8_t *S, uint64_t seed,
+                    uint64_t chain0, uint64_t sweep0, int nsweeps, double beta)
+{
+    for (int k = 0; k < nsweeps; ++k)
+        for (int m = 0; m < M; ++m) {
+            uint8_t *s = S + (size_t)m * L;
+            for (int i = 0; i < L; ++i)
+                s[i] = (uint8_t)orc_metropolis_step(h, J, L, q, s, i, beta, seed, chain0 + (uint64_t)m,
+                                                    sweep0 + (uint64_t)k, NULL);
+        }
+}
+
+/* Teacher-forced check of one Metropolis sweep produced elsewhere, as
+ * orc_gibbs_verify_rec: the oracle conditions on after[j] for j < i and
+ * before[j] for j > i, proposes and decides with the same uniforms and
+ * compares with after[i]; disagreements are counted and recorded. */
+long orc_metropolis_verify_rec(const double *h, const double *J, int L, int q, int M, const uint8_t *before,
+                               const uint8_t *after, uint64_t seed, uint64_t chain0, uint64_t sweep, double beta,
+                               double *max_margin, double *min_margin, long cap, int64_t *rec_chain,
+                               int32_t *rec_site, double *rec_margin, int32_t *rec_got, int32_t *rec_want)
+{
+    uint8_t *s = (uint8_t *)malloc((size_t)L);
+    long bad = 0;
+    double mxm = 0.0, mnm = INFINITY;
+    for (int m = 0; m < M; ++m) {
+        memcpy(s, before + (size_t)m * L, (size_t)L);
+        for (int i = 0; i < L; ++i) {
+            double mg;
+            const int want = orc_metropolis_step(h, J, L, q, s, i, beta, seed, chain0 + (uint64_t)m, sweep, &mg);
+            if (mg < mnm) mnm = mg;
+            const uint8_t got = after[(size_t)m * L + i];
+            if (got != want) {
+                if (bad < cap && rec_chain) {
+                    rec_chain[bad] = m;
+                    rec_site[bad] = i;
+                    rec_margin[bad] = mg;
+                    rec_got[bad] = got;
+                    rec_want[bad] = want;
+                }
+                ++bad;
+                if (mg > mxm) mxm = mg;
+            }
+            s[i] = got;
+        }
+    }
+    free(s);
+    if (max_margin) *max_margin = mxm;
+    if (min_margin) *min_margin = mnm;
+    return bad;
+}
+
+/* ------------------------------------------------------------------------
  * Model statistics from the chains, unweighted (Sec. 2.1: p_i, p_ij are
  * estimated by the chain frequencies).  Integer counts over the upper
  * block triangle i <= j, block (i,j) at index i*L - i*(i-1)/2 + (j-i),
