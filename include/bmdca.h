@@ -193,6 +193,27 @@ int bm_gibbs_sweep(bm_model m, bm_chains c, int nsweeps, float beta, void *strea
  * (BM_ENGINE_*).  BM_EINVAL for an unknown engine. */
 int bm_model_set_engine(bm_model m, int engine);
 
+/* Update rule of the sweeps (Sec. 2.1: the chains are updated by Gibbs or
+ * Metropolis-Hastings steps; the --sampler option of the training and
+ * sampling commands). */
+enum { BM_SAMPLER_GIBBS = 0, BM_SAMPLER_METROPOLIS = 1 };
+
+/*
+ * bm_model_set_sampler -- the update applied at each site by bm_gibbs_sweep,
+ * the batch sweeps and the server's sampling requests for this model.
+ *   BM_SAMPLER_GIBBS (default): s_i redrawn from the conditional (above).
+ *   BM_SAMPLER_METROPOLIS: one Metropolis-Hastings step per site, sites in
+ *     order 0..L-1: proposal a' = k + (k >= s_i), k = floor(u_p (q-1)),
+ *     uniform over the q-1 other symbols, u_p from Philox counter
+ *     (m, sweep, i, 2); accepted iff u_a < exp(beta (H_i(a') - H_i(s_i)))
+ *     (always when that difference is >= 0), u_a from counter (m, sweep, i,
+ *     3), H_i the local field of the current states (FP32); q = 1 keeps
+ *     the state.  All engines but the one-CTA form run it; with
+ *     BM_ENGINE_MMA the two-CTA form is used instead.
+ * BM_EINVAL for an unknown sampler.
+ */
+int bm_model_set_sampler(bm_model m, int sampler);
+
 /* The kernel form bm_gibbs_sweep runs for this model and M chains, with
  * BM_ENGINE_AUTO resolved: BM_ENGINE_SIMT, BM_ENGINE_MMA or
  * BM_ENGINE_MMA_PAIR, written to *engine_out.  BM_EINVAL for a NULL

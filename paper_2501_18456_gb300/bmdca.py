@@ -21,6 +21,7 @@ BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ENUMERIC, BM_ETIMEOUT, BM_EDEVICE, BM_
     0, -1, -2, -3, -4, -5, -6, -7)
 BM_HOST, BM_DEVICE = 0, 1
 BM_ENGINE_SIMT, BM_ENGINE_AUTO, BM_ENGINE_MMA, BM_ENGINE_MMA_PAIR, BM_ENGINE_MMA_PAIR2 = 0, 1, 2, 3, 4
+BM_SAMPLER_GIBBS, BM_SAMPLER_METROPOLIS = 0, 1
 BM_STATS_AUTO, BM_STATS_SIMT, BM_STATS_MMA_BF16, BM_STATS_MMA_FP8 = 0, 1, 2, 3
 BM_FIELDS_FP32, BM_FIELDS_FP16X2, BM_FIELDS_BF16X2 = 0, 1, 2
 BM_REQ_SAMPLE, BM_REQ_SCORE, BM_REQ_SCAN = 1, 2, 3
@@ -60,6 +61,7 @@ SIGNATURES = {
     "bm_chains_shape": (_I, [_P, _P, _P]),
     "bm_gibbs_sweep": (_I, [_P, _P, _I, _F, _P]),
     "bm_model_set_engine": (_I, [_P, _I]),
+    "bm_model_set_sampler": (_I, [_P, _I]),
     "bm_model_sweep_engine": (_I, [_P, _I, _P]),
     "bm_chains_set_stats_engine": (_I, [_P, _I]),
     "bm_chains_device_status": (_I, [_P, _P]),
@@ -223,6 +225,10 @@ def bm_device_status(m: Model, stream=None):
 
 def bm_model_set_engine(m: Model, engine: int):
     _check(lib().bm_model_set_engine(m.handle, engine), "bm_model_set_engine")
+
+
+def bm_model_set_sampler(m: Model, sampler: int):
+    _check(lib().bm_model_set_sampler(m.handle, sampler), "bm_model_set_sampler")
 
 
 def bm_model_sweep_engine(m: Model, M: int) -> int:

@@ -200,6 +200,15 @@ int bm_model_set_engine(bm_model m, int engine)
     return BM_OK;
 }
 
+int bm_model_set_sampler(bm_model m, int sampler)
+{
+    if (!m) return bm_fail(BM_EINVAL, "bm_model_set_sampler: NULL model");
+    if (sampler != BM_SAMPLER_GIBBS && sampler != BM_SAMPLER_METROPOLIS)
+        return bm_fail(BM_EINVAL, "bm_model_set_sampler: unknown sampler %d", sampler);
+    m->sampler = sampler;
+    return BM_OK;
+}
+
 int bm_model_sweep_engine(bm_model m, int M, int *engine_out)
 {
     if (!m || !engine_out || M < 1) return bm_fail(BM_EINVAL, "bm_model_sweep_engine: bad argument");
@@ -378,14 +387,20 @@ int bm_sweep_form(const bm_model_s *m, int M)
 {
     if (m->engine == BM_ENGINE_MMA_PAIR2) return 3;
     if (m->engine == BM_ENGINE_MMA_PAIR) return 2;
-    if (m->engine == BM_ENGINE_MMA) return 1;
+    if (m->engine == BM_ENGINE_MMA) {
+        // the one-CTA form draws Gibbs updates only; Metropolis sweeps run
+        // on the two-CTA form (or the CUDA cores where that does not fit)
+        if (m->sampler == BM_SAMPLER_METROPOLIS) return bm_gibbs_pair_waves(m, M) > 0 ? 2 : 0;
+        return 1;
+    }
     if (m->engine != BM_ENGINE_AUTO) return 0;
     if (!tensor_beats_gather(m->L, m->q, M)) return 0;
     // Among the tensor-core forms (same grid; the one-CTA form was never the
     // fastest): the two-CTA engine (form 2) and the paired-tensor-core form
     // (form 3) trade places with the cluster count.
     const int w3 = bm_gibbs_paired_waves(m, M), w2 = bm_gibbs_pair_waves(m, M);
-    if (w3 == 0) return w2 > 0 ? 2 : (bm_gibbs_mma_chains_per_cta(m, M) > 0 ? 1 : 0);
+    if (w3 == 0)
+        return w2 > 0 ? 2 : (bm_gibbs_mma_chains_per_cta(m, M) > 0 && m->sampler == BM_SAMPLER_GIBBS ? 1 : 0);
     if (w2 == 0) return 3;
     if (bm_gibbs_pair_tm(m)) {
         // form 2 runs its tensor-memory operand form here, 128 chains per

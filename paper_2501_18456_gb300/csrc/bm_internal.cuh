@@ -15,6 +15,7 @@ struct bm_model_s {
     int L = 0, q = 0;
     int device = 0;
     int engine = BM_ENGINE_AUTO;
+    int sampler = BM_SAMPLER_GIBBS;  // update rule of the sweeps (bm_model_set_sampler)
     // Parameters: front buffer is the live model, back buffer receives the
     // next iterate of bm_update (swapped in when the update is applied).
     float *h = nullptr, *J = nullptr;
@@ -122,6 +123,28 @@ __device__ __forceinline__ uint32_t bm_u24(uint64_t seed, uint64_t chain, uint64
                                            uint64_t site, uint64_t tag)
 {
     return (uint32_t)(bm_philox_word0(seed, chain, sweep, site, tag) >> 40);
+}
+
+// Metropolis-Hastings numerators of site `site` (Sec. 2.1): the proposal
+// index k = floor(u24(tag 2) * (q-1) / 2^24) in bits 24-31 (the proposed
+// symbol is k, or k+1 when k >= the current symbol) and the acceptance
+// numerator u24(tag 3) in bits 0-23.
+__device__ __forceinline__ uint32_t bm_mh_word(uint64_t seed, uint64_t chain, uint64_t sweep, uint64_t site, int q)
+{
+    const uint32_t rp = bm_u24(seed, chain, sweep, site, 2), ra = bm_u24(seed, chain, sweep, site, 3);
+    const uint32_t k = q > 1 ? (uint32_t)(((uint64_t)rp * (uint64_t)(q - 1)) >> 24) : 0u;
+    return (k << 24) | ra;
+}
+
+// Metropolis-Hastings decision from the proposed and current symbols'
+// fields scaled by beta*log2(e): accept when d >= 0 or u < 2^d, with
+// u = (w & 0xffffff) / 2^24 (the hardware base-2 exponential, a few ulp).
+__device__ __forceinline__ bool bm_mh_accept(float hp_l2e, float hc_l2e, uint32_t w)
+{
+    const float d = hp_l2e - hc_l2e;
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(d));
+    return d >= 0.0f || (float)(w & 0xffffffu) * 5.9604644775390625e-8f < e;
 }
 
 // Index of the upper-triangle pair block (i <= j).

@@ -168,6 +168,7 @@ struct GibbsArgs {
     uint64_t seed, sweep0, chain0;  // chain0: global index of chain 0 (Philox counter)
     float beta;
     int M, L, q, Lp, bs, jc, nch, ns, cpc, nsweeps;
+    int sampler;  // BM_SAMPLER_GIBBS or BM_SAMPLER_METROPOLIS
 };
 
 // One CTA of a batched launch: the model and chains it works on (h, Jg,
@@ -306,12 +307,25 @@ __global__ void __launch_bounds__(1024, 1) k_gibbs_staged(const GibbsArgs p0, co
             const uint32_t ibase = (uint32_t)(i % p.jc) * jstep;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
+                const uint64_t m = p.chain0 + cta0 + slot0 + r;  // global chain index
+                if (p.sampler == BM_SAMPLER_METROPOLIS) {
+                    // one Metropolis-Hastings step from the current symbol: the
+                    // lanes of the proposed and current symbols hold their fields
+                    const int cur = (int)((og[r * p.Lp + i] - ibase) / rowb);
+                    const uint32_t w = bm_mh_word(p.seed, m, sweep, (uint64_t)i, q);
+                    const int prop = (int)(w >> 24) + ((int)(w >> 24) >= cur ? 1 : 0);
+                    const float l2e = p.beta * 1.4426950408889634f;
+                    const float hp = __shfl_sync(0xffffffffu, acc[r], g * GW + min(prop, q - 1)) * l2e;
+                    const float hc = __shfl_sync(0xffffffffu, acc[r], g * GW + cur) * l2e;
+                    const int pick = (q > 1 && bm_mh_accept(hp, hc, w)) ? prop : cur;
+                    if (a == 0) og[r * p.Lp + i] = ibase + (uint32_t)pick * rowb;
+                    continue;
+                }
                 const float e = (a < q) ? p.beta * acc[r] : -INFINITY;
                 const float mx = group_max<GW>(e);
                 const float w = (a < q) ? expf(e - mx) : 0.0f;
                 const float S = group_inclusive_scan<GW>(w, a);
                 const float tot = __shfl_sync(0xffffffffu, S, q - 1, GW);
-                const uint64_t m = p.chain0 + cta0 + slot0 + r;  // global chain index
                 const uint32_t r24 = bm_u24(p.seed, m, sweep, (uint64_t)i, 0);
                 const float thr = ((float)r24 * 5.9604644775390625e-8f) * tot;  // u * S_total
                 const unsigned bal = __ballot_sync(0xffffffffu, (a < q) && (thr < S)) & gmask;
@@ -457,6 +471,7 @@ int bm_launch_gibbs_simt(const bm_model_s *m, bm_chains_s *c, int nsweeps, float
     a.chain0 = c->chain0;
     a.sweep0 = c->sweep;
     a.beta = beta;
+    a.sampler = m->sampler;
     a.M = c->M;
     a.L = c->L;
     a.q = c->q;
@@ -562,6 +577,7 @@ void fill_items(const bm_batch_s *b, BatchItem *dst, int nsweeps, float beta, ui
         a.chain0 = c->chain0;
         a.sweep0 = c->sweep;
         a.beta = beta;
+    a.sampler = m->sampler;
         a.M = c->M;
         a.L = c->L;
         a.q = c->q;

@@ -195,6 +195,7 @@ struct PairArgs {
     float beta_l2e;   // beta * log2(e): weights exp(beta H) = 2^(beta log2(e) H)
     int M, L, q, Lp, B, nb, nK, X, NC;
     int na, nmma;     // tensor-memory operand form: coupling ring slots, MMA N (block rows rounded up to 16)
+    int sampler;      // BM_SAMPLER_GIBBS or BM_SAMPLER_METROPOLIS
     long long nblocks;
     uint32_t tmem_cols, acc_stride;
 };
@@ -453,6 +454,25 @@ __device__ __forceinline__ int draw_symbol(float (&H)[QC], int q, uint32_t r24)
 #pragma unroll
     for (int a = 0; a < QC; ++a) n += H[a] <= thr ? 1 : 0;
     return min(n, q - 1);
+}
+
+// The new symbol of a site: the Gibbs draw, or the Metropolis-Hastings step
+// from the current symbol `cur` (w = bm_mh_word of the site).  H holds the
+// fields scaled by beta*log2(e), entries past q masked.
+template <int QC>
+__device__ __forceinline__ int update_symbol(float (&H)[QC], int q, int cur, uint32_t w, int sampler)
+{
+    if (sampler != BM_SAMPLER_METROPOLIS) return draw_symbol<QC>(H, q, w);
+    if (q < 2) return cur;
+    int prop = (int)(w >> 24);
+    prop += prop >= cur ? 1 : 0;
+    float hp = 0.0f, hc = 0.0f;
+#pragma unroll
+    for (int a = 0; a < QC; ++a) {
+        hp = a == prop ? H[a] : hp;
+        hc = a == cur ? H[a] : hc;
+    }
+    return bm_mh_accept(hp, hc, w) ? prop : cur;
 }
 
 // BATCH: cluster k runs items[k] (its own model, tensor map and chain tile);
@@ -768,8 +788,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             if (w < NC) {
                 const uint64_t m = p.chain0 + cta0 + w;
                 for (int pp = 0; pp < g.Bk; pp += 2) {
-                    const uint32_t u0 = bm_u24(p.seed, m, sweep, (uint64_t)(g.i0 + pp), 0);
-                    const uint32_t u1 = bm_u24(p.seed, m, sweep, (uint64_t)(g.i0 + pp + 1), 0);
+                    const uint64_t i0 = (uint64_t)(g.i0 + pp);
+                    const uint32_t u0 = p.sampler == BM_SAMPLER_METROPOLIS ? bm_mh_word(p.seed, m, sweep, i0, q)
+                                                                          : bm_u24(p.seed, m, sweep, i0, 0);
+                    const uint32_t u1 = p.sampler == BM_SAMPLER_METROPOLIS ? bm_mh_word(p.seed, m, sweep, i0 + 1, q)
+                                                                          : bm_u24(p.seed, m, sweep, i0 + 1, 0);
                     ur[pp] = u0;
                     if (pp + 1 < g.Bk) ur[pp + 1] = u1;
                 }
@@ -839,7 +862,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     }
 #pragma unroll
                     for (int a = 0; a < QC; ++a) H[a] = a < q ? H[a] * p.beta_l2e : -INFINITY;
-                    st[ch * Sst + i] = (uint8_t)draw_symbol<QC>(H, q, r24);
+                    st[ch * Sst + i] = (uint8_t)update_symbol<QC>(H, q, st[ch * Sst + i], r24, p.sampler);
                 }
                 named_bar_sync(1, kDraw);  // Hs is rewritten for the next site
             }
@@ -1395,8 +1418,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTmThreads, 1)
             const Blk g = blk_of(p, kb);
             const uint64_t sweep = p.sweep0 + (uint64_t)(kb / p.nb);
             for (int pp = 0; pp < g.Bk; pp += 2) {
-                const uint32_t u0 = bm_u24(p.seed, m, sweep, (uint64_t)(g.i0 + pp), 0);
-                const uint32_t u1 = bm_u24(p.seed, m, sweep, (uint64_t)(g.i0 + pp + 1), 0);
+                const uint64_t i0 = (uint64_t)(g.i0 + pp);
+                const uint32_t u0 = p.sampler == BM_SAMPLER_METROPOLIS ? bm_mh_word(p.seed, m, sweep, i0, q)
+                                                                      : bm_u24(p.seed, m, sweep, i0, 0);
+                const uint32_t u1 = p.sampler == BM_SAMPLER_METROPOLIS ? bm_mh_word(p.seed, m, sweep, i0 + 1, q)
+                                                                      : bm_u24(p.seed, m, sweep, i0 + 1, 0);
                 urow[pp] = u0;
                 if (pp + 1 < g.Bk) urow[pp + 1] = u1;
             }
@@ -1460,7 +1486,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTmThreads, 1)
                 }
 #pragma unroll
                 for (int a = 0; a < QC; ++a) H[a] = a < q ? H[a] * p.beta_l2e : -INFINITY;
-                st[ch * Sst + i] = (uint8_t)draw_symbol<QC>(H, q, r24);
+                st[ch * Sst + i] = (uint8_t)update_symbol<QC>(H, q, st[ch * Sst + i], r24, p.sampler);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -1761,6 +1787,7 @@ void fill_args(const bm_model_s *m, const bm_chains_s *c, int NC, int nsweeps, f
     a.tmem_cols = 2 * a.acc_stride;
     a.na = 0;
     a.nmma = 0;
+    a.sampler = m->sampler;
 }
 
 // The shared-memory operand kernel for q rounded up to 8 (CG2: paired tensor cores).

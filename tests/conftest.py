@@ -16,7 +16,7 @@ def pytest_configure(config):
 def pytest_terminal_summary(terminalreporter):
     import fliplog
     if fliplog.CHECKED[0]:
-        terminalreporter.section("Gibbs boundary flips")
+        terminalreporter.section("Boundary flips of the teacher-forced sweep checks")
         for line in fliplog.summary_lines():
             terminalreporter.write_line(line)
 

@@ -13,11 +13,12 @@ FLIPS = []      # dicts: where, chain, site, sweep, margin, got, want
 CHECKED = [0]   # site-updates verified
 
 
-def verify(orc, h, J, before, after, seed, sweep, beta=1.0, chain0=0, where=""):
-    """Teacher-forced check of one sweep; records each disagreement and
-    returns (n_bad, worst_margin)."""
-    bad, _, flips = orc.gibbs_flips(np.asarray(h, np.float64), np.asarray(J, np.float64), before, after,
-                                    seed, sweep, beta, chain0)
+def verify(orc, h, J, before, after, seed, sweep, beta=1.0, chain0=0, where="", metropolis=False):
+    """Teacher-forced check of one sweep (Gibbs, or Metropolis-Hastings);
+    records each disagreement and returns (n_bad, worst_margin)."""
+    check = orc.metropolis_flips if metropolis else orc.gibbs_flips
+    bad, _, flips = check(np.asarray(h, np.float64), np.asarray(J, np.float64), before, after,
+                          seed, sweep, beta, chain0)
     CHECKED[0] += int(np.asarray(before).size)
     worst = 0.0
     for f in flips:
