@@ -48,10 +48,12 @@ L_SITES, Q, M_CHAINS, N_SEQS, NSWEEPS, LR, SEED = 256, 21, 10000, 50000, 10, 0.0
 WORKLOAD = "bmDCA dense protein-like: L=256 q=21 M=10000 chains, 10 sweeps/iter, MSA N=50000"
 METRIC = "Gibbs site-updates/s (L=256,q=21,M=10k)"
 UNIT = "site-updates/s"
-# DRAM bytes per 10-sweep launch of each sweep kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of this bench's launch); None
-# whenever the kernel has changed since it was captured.
-TRAFFIC_GIBBS = {}
+# DRAM bytes per 10-sweep launch of each sweep kernel: dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of a one-sweep launch at this
+# shape, times the 10 sweeps of the bench's launch (the couplings are read
+# once per sweep, so the traffic grows in proportion); absent whenever the
+# kernel has changed since it was captured.
+TRAFFIC_GIBBS = {"k_gibbs_pair": 10 * (122337536 + 3695872)}
 
 
 def parse():
@@ -426,6 +428,11 @@ def run_ours(args, rank, world, local):
 
     # ---- per-row timings of the other steps (one step's worth each)
     rows["gibbs_sweep_ms_per_sweep"] = ms_gibbs / NSWEEPS
+    # the same sweep with Metropolis-Hastings steps (the sampler option)
+    bmdca.bm_model_set_sampler(model, bmdca.BM_SAMPLER_METROPOLIS)
+    bmdca.bm_gibbs_sweep(model, chains, 2, 1.0)
+    rows["metropolis_sweep_ms_per_sweep"] = timed(lambda: bmdca.bm_gibbs_sweep(model, chains, NSWEEPS, 1.0), 2) / NSWEEPS
+    bmdca.bm_model_set_sampler(model, bmdca.BM_SAMPLER_GIBBS)
     rows["chain_stats_ms"] = timed(lambda: bmdca.bm_chain_stats(chains, counts), 5)
     rows["update_pearson_ms"] = timed(lambda: bmdca.bm_update(model, fi, fij, counts, M_CHAINS, LR, 2.0, True), 5)
     n_score = 100000
