@@ -290,6 +290,8 @@ int bm_chains_free(bm_chains c)
     cudaFree(c->s);
     cudaFree(c->derr);
     if (c->xt) cudaFree(c->xt);
+    if (c->ct_ws) cudaFree(c->ct_ws);
+    if (c->ct_cnt) cudaFree(c->ct_cnt);
     delete c;
     return BM_OK;
 }

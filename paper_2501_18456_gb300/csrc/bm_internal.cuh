@@ -71,6 +71,11 @@ struct bm_chains_s {
     // (xt_rows x xt_cols bytes, owned) and its TMA tensor map.
     void *xt = nullptr;
     int xt_rows = 0, xt_cols = 0;
+    // Partial counts of the tiles split along the chains (owned; int32), their
+    // arrival tickets (owned; epoch in the high word) and the last epoch.
+    int32_t *ct_ws = nullptr;
+    unsigned long long *ct_cnt = nullptr;
+    unsigned int ct_epoch = 0;
     alignas(64) unsigned char tmap_a[128] = {};
 };
 
