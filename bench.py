@@ -510,7 +510,7 @@ def run_ours(args, rank, world, local):
     cs_flops = 2.0 * M_CHAINS * (L_SITES * (L_SITES + 1) / 2) * Q * Q
     cs_ach = cs_flops / (rows["chain_stats_ms"] * 1e-3) / 1e12
     roofline_counts = {"bound": "tensor", "achieved": cs_ach, "peak": 2 * peak_tf, "unit": "TFLOP/s",
-                       "frac": cs_ach / (2 * peak_tf), "kernel": "k_onehot_t + k_counts_tc",
+                       "frac": cs_ach / (2 * peak_tf), "kernel": "k_onehot_t + k_counts_pair",
                        "note": "achieved = 2*M*(L(L+1)/2)*q^2 flops / CUDA-event time of bm_chain_stats "
                                "(one-hot build included); peak: fp8 = 2 x " + peak_src + " bf16_tflops (burst)"}
 
