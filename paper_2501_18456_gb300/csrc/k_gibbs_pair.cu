@@ -617,8 +617,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                             break;
                         }
                         const uint32_t dst = su32(base + lay.a + sa * kSlotA), bar = full_a + 8 * sa;
-                        mbar_expect_tx(bar, (uint32_t)kSlotA);
-                        tma_load_3d(dst, tm_jp, 0, r0, 2 * c, bar);  // hi slab then lo slab of 128 rows
+                        if (CG2) {  // both CTAs' tiles count on CTA 0's barrier of the slot
+                            if (r == 0) mbar_expect_tx(bar, 2u * (uint32_t)kSlotA);
+                            tma_load_3d_cg2(dst, tm_jp, 0, r0, 2 * c, peer_addr(bar, 0));
+                        } else {
+                            mbar_expect_tx(bar, (uint32_t)kSlotA);
+                            tma_load_3d(dst, tm_jp, 0, r0, 2 * c, bar);  // hi slab then lo slab of 128 rows
+                        }
                         ++issued;
                         if (++sa == kNA) {
                             sa = 0;
@@ -626,10 +631,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         }
                     }
                 }
-            if (*abort_flag) {
-                volatile int no_abort = 0;
-                for (long long u = issued > kNA ? issued - kNA : 0; u < issued; ++u)
-                    mbar_wait(full_a + 8 * (int)(u % kNA), (uint32_t)((u / kNA) & 1), &no_abort, p.err);
+            if (*abort_flag) {  // let the copies in flight land before exit
+                if (!CG2 || r == 0) {
+                    volatile int no_abort = 0;
+                    for (long long u = issued > kNA ? issued - kNA : 0; u < issued; ++u)
+                        mbar_wait(full_a + 8 * (int)(u % kNA), (uint32_t)((u / kNA) & 1), &no_abort, p.err);
+                } else {
+                    __nanosleep(100000);  // this CTA's tiles are counted on CTA 0's barriers
+                }
             }
         }
     } else if (warp == 1 && CG2) {
@@ -654,8 +663,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                             ok = false;
                             break;
                         }
-                        // CTA 1's coupling tile and one-hot rows of this chunk (relayed by
-                        // its forwarding thread; slot sa of the coupling ring, same phase)
+                        // CTA 1's one-hot rows of this chunk (relayed by its forwarding
+                        // thread; slot sa of the coupling ring, same phase); its coupling
+                        // tile is counted on full_a above
                         if (!mbar_wait_cl(peer_full + 8 * sa, pha, abort_flag, p.err)) {
                             ok = false;
                             break;
@@ -692,9 +702,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 }
             mma_commit_mc(fin, 3);  // teardown waits for every MMA of the launch, in both CTAs
         } else if (lane == 0) {
-            // CTA 1: relay, chunk by chunk, that this CTA's coupling tile and its
-            // one-hot rows are in place (one arrival on CTA 0's barrier of the
-            // chunk's coupling slot).  A slot's barrier cannot move on by two
+            // CTA 1: relay, chunk by chunk, that this CTA's one-hot rows are in
+            // place (one arrival on CTA 0's barrier of the chunk's coupling
+            // slot; its coupling tiles count on CTA 0's full_a directly).  A slot's barrier cannot move on by two
             // phases before CTA 0 has consumed the chunk: the chunk kNA later
             // needs this slot refilled, which waits for that chunk's MMAs.
             const uint32_t pf0 = peer_addr(peer_full, 0);
@@ -702,9 +712,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             for (long long P = 0; P <= npairs; ++P)
                 for (int step = 0; step < 4; ++step) total += seg_info_cg(p, P, step, 1).s.n;
             for (long long k = 0; k < total; ++k) {
-                if (!mbar_wait(full_a + 8 * (int)(k % kNA), (uint32_t)((k / kNA) & 1), abort_flag, p.err) ||
-                    !mbar_wait(full_b + 8 * (int)(k % NB), (uint32_t)((k / NB) & 1), abort_flag, p.err))
-                    break;
+                if (!mbar_wait(full_b + 8 * (int)(k % NB), (uint32_t)((k / NB) & 1), abort_flag, p.err)) break;
                 mbar_arrive_peer_relaxed(pf0 + 8 * (uint32_t)(k % kNA));
             }
         }

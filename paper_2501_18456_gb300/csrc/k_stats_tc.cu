@@ -198,16 +198,6 @@ __device__ __forceinline__ void cluster_sync()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// TMA tile load into this CTA's shared memory whose completion is counted on
-// `bar`, a barrier of either CTA of the pair (shared::cluster address).
-__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
 __device__ __forceinline__ void mma_f8_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
@@ -318,8 +308,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     const uint32_t dst = su32(base + s * (kStageA + kStageB));
                     const uint32_t fb = leader_addr(full + 8 * s);
                     if (r == 0) mbar_expect_tx(full + 8 * s, 2 * (kStageA + kStageB));  // both CTAs' bytes
-                    tma_load_3d_pair(dst, &tm_x, 0, ya, k, fb);
-                    tma_load_3d_pair(dst + kStageA, &tm_x, 0, yb, k, fb);
+                    tma_load_3d_cg2(dst, &tm_x, 0, ya, k, fb);
+                    tma_load_3d_cg2(dst + kStageA, &tm_x, 0, yb, k, fb);
                     ++issued;
                     if (++s == kNS) {
                         s = 0;

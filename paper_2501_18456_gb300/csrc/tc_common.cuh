@@ -88,6 +88,18 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// TMA tile load of a CTA pair (tcgen05 cta_group::2): the tile lands in this
+// CTA's shared memory and its bytes are counted on `bar`, a shared::cluster
+// address of a barrier in either CTA of the pair (the pair's MMA issuer
+// waits on one barrier for both CTAs' tiles).
+__device__ __forceinline__ void tma_load_3d_cg2(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
 // K-major 128B-swizzle matrix descriptor: start >> 4 [0,14), leading offset
 // (unused) [16,30), 8-row groups 1024 bytes apart [32,46), fixed 0b001 at
 // [46,49), layout 2 = 128B swizzle at [61,64).
