@@ -96,7 +96,7 @@ int bm_potts_load(const float *h, const float *J, int L, int q, int where, void 
     LOAD_CK(cudaMalloc(&m->Jg, (size_t)L * L * m->bs * sizeof(float)));
     LOAD_CK(cudaMalloc(&m->dflags, 8 * sizeof(int)));
     LOAD_CK(cudaMemsetAsync(m->dflags, 0, 8 * sizeof(int), st));
-    m->red_cap = (size_t)bm_update_num_partials(L) * 5 + 8;
+    m->red_cap = (size_t)bm_update_num_partials(L, q) * 5 + 8;
     LOAD_CK(cudaMalloc(&m->dred, m->red_cap * sizeof(double)));
     LOAD_CK(cudaMemcpyAsync(m->h, h, nh * sizeof(float), copy_kind(where, BM_DEVICE), st));
     LOAD_CK(cudaMemcpyAsync(m->J, J, nJ * sizeof(float), copy_kind(where, BM_DEVICE), st));
@@ -128,6 +128,7 @@ int bm_potts_load(const float *h, const float *J, int L, int q, int where, void 
         free_model(m);
         return rc;
     }
+    m->jg_current = true;
     *out = m;
     return BM_OK;
 }
@@ -161,7 +162,7 @@ int bm_potts_set(bm_model m, const float *h, const float *J, int where, void *st
         m->mma_current = false;
         m->bf_current = false;
         m->corr_current = false;
-        return bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
+        m->jg_current = false;
     }
     return BM_OK;
 }
@@ -417,9 +418,21 @@ int bm_sweep_form(const bm_model_s *m, int M)
     return (long long)m->L * m->q * m->q < 90000 ? 3 : 2;
 }
 
+int bm_gather_prepare(bm_model_s *m, cudaStream_t st)
+{
+    if (m->jg_current) return BM_OK;
+    const int rc = bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
+    if (rc == BM_OK) m->jg_current = true;
+    return rc;
+}
+
 int bm_sweep_run(bm_model_s *m, bm_chains_s *c, int nsweeps, float beta, cudaStream_t st)
 {
     const int form = bm_sweep_form(m, c->M);
+    if (form == 0) {  // the CUDA-core sweep reads the gather layout
+        const int rc = bm_gather_prepare(m, st);
+        if (rc != BM_OK) return rc;
+    }
     for (int done = 0; done < nsweeps;) {
         const int k = nsweeps - done < kMaxSweepsPerLaunch ? nsweeps - done : kMaxSweepsPerLaunch;
         const int rc = form == 3   ? bm_launch_gibbs_paired(m, c, k, beta, st)
@@ -521,7 +534,7 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
     if (M < 1) return bm_fail(BM_EINVAL, "bm_update: M=%d < 1", M);
     if (!isfinite(lr)) return bm_fail(BM_EINVAL, "bm_update: lr not finite");
     cudaStream_t st = (cudaStream_t)stream;
-    const int nparts = bm_update_num_partials(m->L);
+    const int nparts = bm_update_num_partials(m->L, m->q);
     double *partials = m->dred;
     double *moments = m->dred + (size_t)nparts * 5;
     const int want = pearson_out != nullptr;
@@ -551,8 +564,7 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
         m->mma_current = false;
         m->bf_current = false;
         m->corr_current = false;
-        rc = bm_launch_build_gather(m->J, m->Jg, m->L, m->q, st);
-        if (rc != BM_OK) return rc;
+        m->jg_current = false;  // rebuilt by the next reader of the gather layout
     }
     if (applied_out) *applied_out = apply ? 1 : 0;
     return BM_OK;
@@ -562,6 +574,8 @@ int bm_energy_score(bm_model m, const uint8_t *seqs_dev, int n, float *E_dev, vo
 {
     if (!m || (n > 0 && (!seqs_dev || !E_dev))) return bm_fail(BM_EINVAL, "bm_energy_score: NULL argument");
     if (n < 0) return bm_fail(BM_EINVAL, "bm_energy_score: n=%d < 0", n);
+    const int rc = bm_gather_prepare(m, (cudaStream_t)stream);
+    if (rc != BM_OK) return rc;
     return bm_launch_energy(m, seqs_dev, n, E_dev, m->dflags + 4, (cudaStream_t)stream);
 }
 
@@ -571,7 +585,10 @@ int bm_fields(bm_model m, const uint8_t *seqs_dev, int n, float *H_dev, int form
     if (n < 0) return bm_fail(BM_EINVAL, "bm_fields: n=%d < 0", n);
     cudaStream_t st = (cudaStream_t)stream;
     switch (form) {
-    case BM_FIELDS_FP32: return bm_launch_fields_simt(m, seqs_dev, n, H_dev, st);
+    case BM_FIELDS_FP32: {
+        const int rc = bm_gather_prepare(m, st);
+        return rc != BM_OK ? rc : bm_launch_fields_simt(m, seqs_dev, n, H_dev, st);
+    }
     case BM_FIELDS_FP16X2: return bm_launch_fields_tc(m, seqs_dev, n, H_dev, 0, st);
     case BM_FIELDS_BF16X2: return bm_launch_fields_tc(m, seqs_dev, n, H_dev, 1, st);
     default: return bm_fail(BM_EINVAL, "bm_fields: unknown form %d", form);

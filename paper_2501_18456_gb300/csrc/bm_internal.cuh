@@ -21,9 +21,11 @@ struct bm_model_s {
     float *h = nullptr, *J = nullptr;
     float *h_back = nullptr, *J_back = nullptr;
     // Gather layout of the live J: Jg[i][j][b][a] = J_ij(a,b), each (i,j)
-    // block padded to bs floats (16-byte aligned blocks).
+    // block padded to bs floats (16-byte aligned blocks).  Read by the
+    // CUDA-core forms only; rebuilt lazily (bm_gather_prepare) when stale.
     float *Jg = nullptr;
     int bs = 0;
+    bool jg_current = false;
     // Tensor-core layout of the live J: fp16 hi/lo parts, 128 rows per site
     // block (rows (i,a) of the block, zero padded), Kp columns (j,b) (zero
     // padded to a multiple of 64) in 64-column slabs with hi and lo
@@ -158,6 +160,58 @@ __host__ __device__ __forceinline__ size_t bm_pair_block(int L, int i, int j)
     return (size_t)i * L - (size_t)i * (i - 1) / 2 + (size_t)(j - i);
 }
 
+// Row tiles of the upper pair triangle: row i holds the q x q blocks
+// (i, j) for j = i+1..L-1, contiguous in J, f_ij and the counts; a tile is
+// K whole blocks of one row.  Tiles of rows with n = 1..N blocks:
+// sum over n of ceil(n / K).
+__host__ __device__ inline long long bm_row_tiles_upto(long long N, int K)
+{
+    const long long a = N / K, b = N - a * K;
+    return (long long)K * a * (a + 1) / 2 + b * (a + 1);
+}
+
+// Tile t -> row i and its first block jj0 (rows in order: the rows before
+// row i hold T(L-1) - T(L-1-i) tiles); binary search over the rows.
+__host__ __device__ inline void bm_row_tile(long long t, int L, int K, int &i, int &jj0)
+{
+    const long long TL = bm_row_tiles_upto(L - 1, K);
+    int lo = 0, hi = L - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (TL - bm_row_tiles_upto(L - 1 - mid, K) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    i = lo;
+    jj0 = (int)(t - (TL - bm_row_tiles_upto(L - 1 - lo, K))) * K;
+}
+
+// Position (jj, a, b) of element e = jj q^2 + a q + b, advanced by a fixed
+// step (djj, da, db) without divisions (each carry at most one).
+struct BmPos3 {
+    int jj, a, b;
+    __device__ __forceinline__ void init(int e, int q, int qq)
+    {
+        jj = e / qq;
+        const int w = e - jj * qq;
+        a = w / q;
+        b = w - a * q;
+    }
+    __device__ __forceinline__ void step(int djj, int da, int db, int q)
+    {
+        b += db;
+        if (b >= q) {
+            b -= q;
+            ++a;
+        }
+        a += da;
+        if (a >= q) {
+            a -= q;
+            ++jj;
+        }
+        jj += djj;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (each returns BM_OK or an error code)
 // ---------------------------------------------------------------------------
@@ -210,7 +264,9 @@ int bm_launch_weight_sum(const float *w, int N, double *out2, cudaStream_t st);
 int bm_launch_update(bm_model_s *m, const float *fi, const float *fij, const int32_t *counts,
                      int M, float lr, int want_pearson, double *partials, int nparts,
                      double *moments, cudaStream_t st);
-int bm_update_num_partials(int L);
+int bm_update_num_partials(int L, int q);
+// Rebuilds the gather layout Jg from the live J on `st` when it is stale.
+int bm_gather_prepare(bm_model_s *m, cudaStream_t st);
 int bm_launch_energy(const bm_model_s *m, const uint8_t *seqs, int n, float *E, int *bad, cudaStream_t st);
 int bm_launch_energy_gather(const float *h, const float *J, int L, int q, const uint8_t *seqs, int n,
                             float *E, int *bad, cudaStream_t st);

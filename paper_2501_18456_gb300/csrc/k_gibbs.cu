@@ -649,6 +649,10 @@ int prepare(bm_batch_s *b, cudaStream_t st)
 
 int launch_graph(bm_batch_s *b, int nsweeps, float beta, cudaStream_t st, uint8_t *const *states_override)
 {
+    for (bm_model_s *m : b->models) {  // the CUDA-core batch reads each model's gather layout
+        const int rc = bm_gather_prepare(m, st);
+        if (rc != BM_OK) return rc;
+    }
     const int k = b->next;
     b->next ^= 1;
     BM_CK(cudaEventSynchronize(b->used[k]));  // the previous launch that read this host copy has run

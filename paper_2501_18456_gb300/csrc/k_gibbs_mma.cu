@@ -660,31 +660,42 @@ __device__ __forceinline__ float from_t(__nv_bfloat16 v) { return __bfloat162flo
 // +-65504 (so the operands stay finite) and flagged in *ovf; the model's
 // status call then reports BM_ENUMERIC for the tensor-core sweep.
 template <typename T>
-__global__ void k_build_mma_layout(const float *__restrict__ J, T *__restrict__ jt, int L, int q, int Kp, int B, int nb,
-                                   int *__restrict__ ovf)
+__global__ void __launch_bounds__(256) k_build_mma_layout(const float *__restrict__ J, T *__restrict__ jt, int L, int q,
+                                                          int Kp, int B, int nb, int *__restrict__ ovf)
 {
+    // One CTA per output row r = (block, site pp of the block, symbol a);
+    // thread t writes columns k = t + 256 m, whose (j, b) it advances without
+    // divisions.  Row (i, a) of J is J[i][j][a][b] = src[j q^2 + b].
     constexpr bool kHalf = sizeof(T) == 2 && std::is_same<T, __half>::value;
-    const size_t rows = (size_t)nb * kRowsA, n = rows * Kp;
-    const int Q = L * q;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = t / Kp;
-        const int k = (int)(t - r * Kp);
-        const int blk = (int)(r / kRowsA), rr = (int)(r % kRowsA);
-        const int pp = rr / q, a = rr % q, i = blk * B + pp;
+    const int r = blockIdx.x;
+    const int blk = r / kRowsA, rr = r - blk * kRowsA;
+    const int pp = rr / q, a = rr - pp * q, i = blk * B + pp;
+    const bool row_ok = pp < B && i < L;
+    const int Q = L * q, qq = q * q;
+    const float *src = J + ((size_t)(row_ok ? i : 0) * L * q + a) * q;
+    T *out = jt + (size_t)r * (2 * Kp);
+    const int dj = 256 / q, db = 256 - dj * q;
+    int k = threadIdx.x, j = k / q, b = k - j * q;
+    int bad = 0;
+    for (; k < Kp; k += 256) {
         float v = 0.0f;
-        if (k < Q && pp < B && i < L) {
-            const int j = k / q, b = k % q;
-            v = J[(((size_t)i * L + j) * q + a) * q + b];
-        }
+        if (row_ok && k < Q) v = src[(size_t)j * qq + b];
         if (kHalf && !(fabsf(v) <= 65504.0f)) {
-            atomicOr(ovf, 1);
+            bad = 1;
             v = v != v ? 0.0f : copysignf(65504.0f, v);
         }
         const T vh = to_t(v, (T *)nullptr);
-        const size_t o = r * (size_t)(2 * Kp) + (size_t)(k / kKC) * (2 * kKC) + (k % kKC);
-        jt[o] = vh;
-        jt[o + kKC] = to_t(v - from_t(vh), (T *)nullptr);
+        const int o = ((k / kKC) * (2 * kKC)) + (k % kKC);  // slab k/64: hi then lo
+        out[o] = vh;
+        out[o + kKC] = to_t(v - from_t(vh), (T *)nullptr);
+        b += db;
+        if (b >= q) {
+            b -= q;
+            ++j;
+        }
+        j += dj;
     }
+    if (bad) atomicOr(ovf, 1);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -786,8 +797,7 @@ int bm_split_prepare(bm_model_s *m, int bf16, cudaStream_t st)
         }
         if (rc != BM_OK) return rc;
     }
-    const size_t n = (size_t)rows * Kp;
-    const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 64);
+    const int grid = rows;
     if (bf16)
         k_build_mma_layout<__nv_bfloat16><<<grid, 256, 0, st>>>(m->J, (__nv_bfloat16 *)*buf, m->L, m->q, Kp, B, nb,
                                                                  m->dflags + 5);

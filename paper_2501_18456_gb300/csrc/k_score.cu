@@ -6,28 +6,55 @@
 namespace {
 
 // Flags: bit 0 asymmetric J, bit 1 nonzero J_ii, bit 2 non-finite value.
-__global__ void k_check_model(const float *__restrict__ h, const float *__restrict__ J, int L,
-                              int q, int *flags)
+// The upper pair blocks (i, j > i) are taken in row tiles of K whole blocks
+// (contiguous in J); a tile is staged in shared memory and its transposed
+// partners (j, i) are read in their own order, so both reads are coalesced.
+// Diagonal blocks and h are checked by a grid-stride pass.
+constexpr int kChkElems = 4096;
+
+__host__ __device__ inline int chk_blocks_per_tile(int q) { return max(1, kChkElems / (q * q)); }
+
+__global__ void __launch_bounds__(256) k_check_model(const float *__restrict__ h, const float *__restrict__ J, int L,
+                                                     int q, long long ntiles, int *flags)
 {
-    const size_t n = (size_t)L * L * q * q;
-    const size_t qq = (size_t)q * q;
+    __shared__ float tile[kChkElems];
+    const int qq = q * q, K = chk_blocks_per_tile(q);
+    const int tid = threadIdx.x;
     int f = 0;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (size_t)gridDim.x * blockDim.x) {
-        const size_t blk = t / qq, e = t % qq;
-        const int i = (int)(blk / L), j = (int)(blk % L);
-        const int a = (int)(e / q), b = (int)(e % q);
-        const float v = J[t];
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + tid; t < (size_t)L * q; t += stride)
+        if (!isfinite(h[t])) f |= 4;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + tid; t < (size_t)L * qq; t += stride) {
+        const size_t i = t / qq, e = t - i * qq;
+        const float v = J[(i * L + i) * qq + e];
         if (!isfinite(v)) f |= 4;
-        if (i == j) {
-            if (v != 0.0f) f |= 2;
-        } else if (i < j) {
-            const float w = J[(((size_t)j * L + i) * q + b) * q + a];
-            if (!(v == w) && isfinite(v) && isfinite(w)) f |= 1;
-        }
-        if (t < (size_t)L * q && !isfinite(h[t])) f |= 4;
+        if (v != 0.0f) f |= 2;
     }
-    if (f) atomicOr(flags, f);
+    const int djj = 256 / qq, rem = 256 - djj * qq, da = rem / q, db = rem - da * q;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int i, jj0;
+        bm_row_tile(t, L, K, i, jj0);
+        const int nel = min(K, L - 1 - i - jj0) * qq, j0 = i + 1 + jj0;
+        const float *src = J + ((size_t)i * L + j0) * qq;
+        for (int e = tid; e < nel; e += 256) {
+            const float v = src[e];
+            tile[e] = v;
+            if (!isfinite(v)) f |= 4;
+        }
+        __syncthreads();
+        BmPos3 pt;  // (jj, b, a) of index d = jj q^2 + b q + a in the transposed blocks
+        pt.init(tid, q, qq);
+        for (int d = tid; d < nel; d += 256) {
+            const float w = J[((size_t)(j0 + pt.jj) * L + i) * qq + (d - pt.jj * qq)];
+            const float v = tile[pt.jj * qq + pt.b * q + pt.a];
+            if (!isfinite(w)) f |= 4;
+            else if (isfinite(v) && !(v == w)) f |= 1;
+            pt.step(djj, da, db, q);
+        }
+        __syncthreads();  // the tile is rewritten by the next one
+    }
+    f = __reduce_or_sync(0xffffffffu, f);
+    if (f && (tid & 31) == 0) atomicOr(flags, f);
 }
 
 __global__ void k_check_symbols(const uint8_t *__restrict__ s, size_t n, int q, int *flag)
@@ -99,9 +126,9 @@ int bm_launch_check_model(const float *h, const float *J, int L, int q, int *dfl
                           cudaStream_t st)
 {
     BM_CK(cudaMemsetAsync(dflags, 0, sizeof(int), st));
-    const size_t n = (size_t)L * L * q * q;
-    const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
-    k_check_model<<<std::max(grid, 1), 256, 0, st>>>(h, J, L, q, dflags);
+    const long long ntiles = L >= 2 ? bm_row_tiles_upto(L - 1, chk_blocks_per_tile(q)) : 0;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(std::max<long long>(ntiles, (long long)L * q * q / 256 + 1), 1216));
+    k_check_model<<<grid, 256, 0, st>>>(h, J, L, q, ntiles, dflags);
     BM_CK_LAUNCH("k_check_model");
     return BM_OK;
 }

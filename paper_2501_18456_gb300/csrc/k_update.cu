@@ -1,45 +1,42 @@
 // Boltzmann-learning step (Eq. 5) fused with the Pearson convergence
 // check (Sec. 2.1, "Convergence criterium").
 //
-// One warp per site pair i < j walks the q*q entries of the pair block:
+// For every site pair i < j and symbols a, b:
 //   p_ij = C_ij / M,  p_i = C_ii(a,a) / M                (chain frequencies)
 //   J'_ij(a,b) = J_ij(a,b) + lr (f_ij(a,b) - p_ij(a,b))  written to (i,j,a,b)
 //                                                        and (j,i,b,a)
 //   x = f_ij - f_i f_j,  y = p_ij - p_i p_j              (connected correlations)
-// and accumulates sum x, y, x^2, y^2, xy (x and y themselves are FP32, the
-// precision of their inputs): within a pair each lane adds its terms with
-// Kahan-compensated FP32 sums, and the pairs are reduced in FP64.  The
-// transposed (j,i) copy goes through a per-warp shared-memory tile so both
-// writes are coalesced.  Per-CTA partial moments go to a scratch array that
-// a single-CTA kernel sums in a fixed order, so the result is
-// deterministic.  The new parameters go to the back buffer; the
-// host decides whether to swap it in.
+// and the sums of x, y, x^2, y^2, xy.  The pair blocks (i, j > i) of site i
+// are contiguous in J, f_ij and the counts, so the kernel streams these row
+// segments: a CTA takes K whole blocks of one row at a time (K q^2 <= 4096
+// elements), each thread loading up to 16 elements of each array with
+// independent coalesced loads.  The new blocks are staged in shared memory
+// and their transposed (j,i) copies are written in destination order, so
+// both writes are coalesced.  Each thread adds its x, y terms with
+// Kahan-compensated FP32 sums (x and y themselves are FP32, the precision
+// of their inputs), the threads are reduced in FP64, and the per-CTA partial
+// moments go to a scratch array that a single-CTA kernel sums in a fixed
+// order, so the result is deterministic.  The new parameters go to the back
+// buffer; the host decides whether to swap it in.
 #include "bm_internal.cuh"
 
 #include <math.h>
 
 namespace {
 
-constexpr int kUpdWarps = 8;
+constexpr int kUpdThreads = 256;
+constexpr int kUpdElems = 4096;  // elements per tile (K whole q x q blocks)
 
-__device__ __forceinline__ void pair_from_index(long long p, int L, int &i, int &j)
+// K whole blocks per tile: K q^2 <= kUpdElems elements and K q <= kUpdElems / 2
+// entries of the f_j, p_j tables (the second bound matters only for q = 1).
+__host__ __device__ inline int upd_blocks_per_tile(int q)
 {
-    // Rows i hold L-1-i pairs; start(i) = i*(2L-i-1)/2.
-    // FP32 estimate of the row; the two loops below make it exact
-    const float tL = 2.0f * (float)L - 1.0f;
-    int r = (int)floorf((tL - sqrtf(fmaxf(tL * tL - 8.0f * (float)p, 0.0f))) * 0.5f);
-    if (r < 0) r = 0;
-    if (r > L - 2) r = L - 2;
-    auto start = [L](long long rr) { return rr * (2LL * L - rr - 1) / 2; };
-    while (r > 0 && start(r) > p) --r;
-    while (r < L - 2 && start(r + 1) <= p) ++r;
-    i = r;
-    j = (int)(p - start(r)) + r + 1;
+    return max(1, min(kUpdElems / (q * q), kUpdElems / 2 / q));
 }
 
 // Kahan-compensated FP32 accumulator: s - c carries the sum to about one
-// ulp whatever the number of terms (used for the ~q*q/32 terms a lane adds
-// per pair before the FP64 reduction across pairs).
+// ulp whatever the number of terms (each thread adds the terms of its
+// elements before the FP64 reduction across threads).
 struct Kahan {
     float s = 0.0f, c = 0.0f;
     __device__ __forceinline__ void add(float x)
@@ -52,89 +49,86 @@ struct Kahan {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-__global__ void __launch_bounds__(kUpdWarps * 32) k_update_pairs(
+__global__ void __launch_bounds__(kUpdThreads) k_update_rows(
     const float *__restrict__ J, float *__restrict__ Jn, const float *__restrict__ fi,
     const float *__restrict__ fij, const int32_t *__restrict__ C, int L, int q, float invM,
-    float lr, int want_pearson, double *__restrict__ partials)
+    float lr, int want_pearson, long long ntiles, double *__restrict__ partials)
 {
-    // per warp: the new (i,j) block for its transposed copy (row stride 33:
-    // conflict-free both ways), and the pair's one-site vectors
-    __shared__ float tile[kUpdWarps][32 * 33];
-    __shared__ float vec[kUpdWarps][4][32];  // p_i(a), p_j(b), f_i(a), f_j(b)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int qq = q * q;
-    const long long P = (long long)L * (L - 1) / 2;
-    float *tw = tile[warp];
-    double sx = 0.0, sy = 0.0, sxx = 0.0, syy = 0.0, sxy = 0.0;
-    for (long long p = (long long)blockIdx.x * kUpdWarps + warp; p < P;
-         p += (long long)gridDim.x * kUpdWarps) {
-        int i, j;
-        pair_from_index(p, L, i, j);
-        const size_t blk = bm_pair_block(L, i, j) * qq;
-        const size_t ij = ((size_t)i * L + j) * qq, ji = ((size_t)j * L + i) * qq;
-        if (want_pearson && lane < q) {
-            vec[warp][0][lane] = (float)C[bm_pair_block(L, i, i) * qq + (size_t)lane * (q + 1)] * invM;
-            vec[warp][1][lane] = (float)C[bm_pair_block(L, j, j) * qq + (size_t)lane * (q + 1)] * invM;
-            vec[warp][2][lane] = fi[(size_t)i * q + lane];
-            vec[warp][3][lane] = fi[(size_t)j * q + lane];
+    __shared__ float tile[kUpdElems];           // new J of the tile's blocks, (jj, a, b) order
+    __shared__ float fj[kUpdElems / 2], pj[kUpdElems / 2];  // f_j(b), p_j(b) of the tile's blocks
+    __shared__ float frow[32], prow[32];        // f_i(a), p_i(a)
+    const int qq = q * q, K = upd_blocks_per_tile(q);
+    const int tid = threadIdx.x;
+    // step of kUpdThreads elements in (jj, a, b) and in transposed (jj, b, a) order
+    const int djj = kUpdThreads / qq, rem = kUpdThreads - djj * qq, da = rem / q, db = rem - da * q;
+    Kahan kx, ky, kxx, kyy, kxy;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int i, jj0;
+        bm_row_tile(t, L, K, i, jj0);
+        const int nb = min(K, L - 1 - i - jj0);
+        const int nel = nb * qq;
+        const int j0 = i + 1 + jj0;
+        if (want_pearson) {
+            for (int k = tid; k < q; k += kUpdThreads) {
+                frow[k] = fi[(size_t)i * q + k];
+                prow[k] = (float)C[bm_pair_block(L, i, i) * qq + (size_t)k * (q + 1)] * invM;
+            }
+            for (int k = tid; k < nb * q; k += kUpdThreads) {
+                const int jj = k / q, bb = k - jj * q;
+                fj[k] = fi[(size_t)(j0 + jj) * q + bb];
+                pj[k] = (float)C[bm_pair_block(L, j0 + jj, j0 + jj) * qq + (size_t)bb * (q + 1)] * invM;
+            }
+            __syncthreads();
         }
-        __syncwarp();
-        Kahan kx, ky, kxx, kyy, kxy;
+        const size_t baseJ = ((size_t)i * L + j0) * qq, baseC = bm_pair_block(L, i, j0) * qq;
+        BmPos3 ps;
+        ps.init(tid, q, qq);
 #pragma unroll 4
-        for (int e = lane; e < qq; e += 32) {
-            const int a = e / q, b = e - a * q;
-            const float f = fij[ij + e];
-            const float pij = (float)C[blk + e] * invM;
-            const float v = fmaf(lr, f - pij, J[ij + e]);
-            Jn[ij + e] = v;
-            tw[a * 33 + b] = v;
+        for (int e = tid; e < nel; e += kUpdThreads) {
+            const float f = fij[baseJ + e];
+            const float pij = (float)C[baseC + e] * invM;
+            const float v = fmaf(lr, f - pij, J[baseJ + e]);
+            Jn[baseJ + e] = v;
+            tile[e] = v;
             if (want_pearson) {
-                const float x = fmaf(-vec[warp][2][a], vec[warp][3][b], f);
-                const float y = fmaf(-vec[warp][0][a], vec[warp][1][b], pij);
+                const float x = fmaf(-frow[ps.a], fj[ps.jj * q + ps.b], f);
+                const float y = fmaf(-prow[ps.a], pj[ps.jj * q + ps.b], pij);
                 kx.add(x);
                 ky.add(y);
                 kxx.add(x * x);
                 kyy.add(y * y);
                 kxy.add(x * y);
             }
+            ps.step(djj, da, db, q);
         }
-        __syncwarp();
+        __syncthreads();
+        // transposed copies: block (j, i) element u = b q + a is J'_ij(a, b)
+        BmPos3 pt;  // (jj, b, a) of destination index d = jj q^2 + b q + a
+        pt.init(tid, q, qq);
 #pragma unroll 4
-        for (int e = lane; e < qq; e += 32) {  // (j,i) block: element (b,a) = J'_ij(a,b)
-            const int b = e / q, a = e - b * q;
-            Jn[ji + e] = tw[a * 33 + b];
+        for (int d = tid; d < nel; d += kUpdThreads) {
+            Jn[((size_t)(j0 + pt.jj) * L + i) * qq + (d - pt.jj * qq)] = tile[pt.jj * qq + pt.b * q + pt.a];
+            pt.step(djj, da, db, q);
         }
-        __syncwarp();  // tile and vec are rewritten by the next pair
-        if (want_pearson) {
-            sx += kx.value();
-            sy += ky.value();
-            sxx += kxx.value();
-            syy += kyy.value();
-            sxy += kxy.value();
-        }
+        __syncthreads();  // tile and the tables are rewritten by the next tile
     }
     if (!want_pearson) return;
+    double m5[5] = {kx.value(), ky.value(), kxx.value(), kyy.value(), kxy.value()};
+    __shared__ double red[kUpdThreads / 32][5];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        sxx += __shfl_xor_sync(0xffffffffu, sxx, o);
-        syy += __shfl_xor_sync(0xffffffffu, syy, o);
-        sxy += __shfl_xor_sync(0xffffffffu, sxy, o);
+    for (int k = 0; k < 5; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m5[k] += __shfl_xor_sync(0xffffffffu, m5[k], o);
     }
-    __shared__ double red[kUpdWarps][5];
-    if (lane == 0) {
-        red[warp][0] = sx;
-        red[warp][1] = sy;
-        red[warp][2] = sxx;
-        red[warp][3] = syy;
-        red[warp][4] = sxy;
-    }
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) red[warp][k] = m5[k];
     __syncthreads();
-    if (threadIdx.x < 5) {
+    if (tid < 5) {
         double s = 0.0;
-        for (int w = 0; w < kUpdWarps; ++w) s += red[w][threadIdx.x];
-        partials[(size_t)blockIdx.x * 5 + threadIdx.x] = s;
+        for (int w = 0; w < kUpdThreads / 32; ++w) s += red[w][tid];
+        partials[(size_t)blockIdx.x * 5 + tid] = s;
     }
 }
 
@@ -149,18 +143,26 @@ __global__ void k_update_fields(const float *__restrict__ h, float *__restrict__
     hn[k] = fmaf(lr, fi[k] - pa, h[k]);
 }
 
-// Sum the per-CTA partials in a fixed order (one CTA, 5 moments).
-__global__ void k_sum_partials(const double *__restrict__ partials, int nparts, double *out5)
+// Sum the per-CTA partials in a fixed order (one CTA, 5 moments): each
+// thread adds its strided share of all five with independent loads, then a
+// fixed-order tree over the threads.
+__global__ void __launch_bounds__(256) k_sum_partials(const double *__restrict__ partials, int nparts, double *out5)
 {
     __shared__ double red[5][256];
-    for (int m = 0; m < 5; ++m) {
-        double s = 0.0;
-        for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += partials[(size_t)k * 5 + m];
-        red[m][threadIdx.x] = s;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+        double v[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) v[m] = partials[(size_t)k * 5 + m];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) acc[m] += v[m];
     }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) red[m][threadIdx.x] = acc[m];
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o)
+#pragma unroll
             for (int m = 0; m < 5; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + o];
         __syncthreads();
     }
@@ -169,11 +171,15 @@ __global__ void k_sum_partials(const double *__restrict__ partials, int nparts, 
 
 }  // namespace
 
-int bm_update_num_partials(int L)
+long long bm_update_num_tiles(int L, int q)
 {
-    const long long P = (long long)L * (L - 1) / 2;
-    long long blocks = (P + kUpdWarps - 1) / kUpdWarps;
-    if (blocks > 1216) blocks = 1216;  // 8 CTAs per SM on 152 SMs
+    return L >= 2 ? bm_row_tiles_upto(L - 1, upd_blocks_per_tile(q)) : 0;
+}
+
+int bm_update_num_partials(int L, int q)
+{
+    long long blocks = bm_update_num_tiles(L, q);
+    if (blocks > 608) blocks = 608;  // 4 CTAs per SM on 152 SMs, ~6 tiles each (measured best of 608 and 912)
     if (blocks < 1) blocks = 1;
     return (int)blocks;
 }
@@ -185,9 +191,9 @@ int bm_launch_update(bm_model_s *m, const float *fi, const float *fij, const int
     const int L = m->L, q = m->q;
     const float invM = 1.0f / (float)M;
     if (L >= 2) {
-        k_update_pairs<<<nparts, kUpdWarps * 32, 0, st>>>(m->J, m->J_back, fi, fij, counts, L, q,
-                                                          invM, lr, want_pearson, partials);
-        BM_CK_LAUNCH("k_update_pairs");
+        k_update_rows<<<nparts, kUpdThreads, 0, st>>>(m->J, m->J_back, fi, fij, counts, L, q, invM, lr,
+                                                      want_pearson, bm_update_num_tiles(L, q), partials);
+        BM_CK_LAUNCH("k_update_rows");
     }
     k_update_fields<<<(L * q + 255) / 256, 256, 0, st>>>(m->h, m->h_back, fi, counts, L, q, invM,
                                                          lr);

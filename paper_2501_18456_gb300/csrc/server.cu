@@ -109,7 +109,8 @@ int launch(bm_server_s *s, Req *rq, cudaStream_t st, cudaEvent_t ev)
         uint8_t *seq = d;
         float *E = reinterpret_cast<float *>(d + round256((size_t)r.n * L));
         e = cudaMemcpyAsync(seq, r.in, (size_t)r.n * L, cudaMemcpyDefault, st);
-        if (e == cudaSuccess) rc = bm_launch_energy(m, seq, r.n, E, m->dflags + 4, st);
+        if (e == cudaSuccess) rc = bm_gather_prepare(m, st);
+        if (e == cudaSuccess && rc == BM_OK) rc = bm_launch_energy(m, seq, r.n, E, m->dflags + 4, st);
         if (rc == BM_OK && e == cudaSuccess) e = cudaMemcpyAsync(r.out, E, (size_t)r.n * 4, cudaMemcpyDefault, st);
         break;
     }
@@ -255,16 +256,17 @@ int bm_server_destroy(bm_server s)
 int bm_server_add_model(bm_server s, bm_model m, int *id)
 {
     if (!s || !m || !id) return bm_fail(BM_EINVAL, "bm_server_add_model: NULL argument");
-    // The tensor-core layouts (split J, in-block corrections) are built here,
-    // once and synchronously: requests run on different streams, so a layout
-    // built lazily by one request could be read by a concurrent one before
-    // its build kernel ran.  Built for every model a tensor-core form could
-    // serve (AUTO's choice depends on each request's chain count).
+    // The lazily built layouts (gather layout, split J, in-block corrections)
+    // are brought up to date here, once and synchronously: requests run on
+    // different streams, so a layout built lazily by one request could be
+    // read by a concurrent one before its build kernel ran.  The tensor-core
+    // ones are built for every model a tensor-core form could serve (AUTO's
+    // choice depends on each request's chain count).
     cudaStream_t st = nullptr;
     BM_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    int rc = BM_OK;
+    int rc = bm_gather_prepare(m, st);
     const bool tc = m->engine != BM_ENGINE_SIMT && m->q >= 2;
-    if (tc && (bm_gibbs_mma_chains_per_cta(m, 1) > 0 || bm_gibbs_pair_chains_per_cluster(m, 1) > 0)) {
+    if (rc == BM_OK && tc && (bm_gibbs_mma_chains_per_cta(m, 1) > 0 || bm_gibbs_pair_chains_per_cluster(m, 1) > 0)) {
         rc = bm_split_prepare(m, 0, st);
         if (rc == BM_OK) rc = bm_corr_prepare(m, st);
     }
