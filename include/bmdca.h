@@ -215,8 +215,8 @@ enum { BM_SAMPLER_GIBBS = 0, BM_SAMPLER_METROPOLIS = 1 };
 int bm_model_set_sampler(bm_model m, int sampler);
 
 /* The kernel form bm_gibbs_sweep runs for this model and M chains, with
- * BM_ENGINE_AUTO resolved: BM_ENGINE_SIMT, BM_ENGINE_MMA or
- * BM_ENGINE_MMA_PAIR, written to *engine_out.  BM_EINVAL for a NULL
+ * BM_ENGINE_AUTO resolved: BM_ENGINE_SIMT, BM_ENGINE_MMA,
+ * BM_ENGINE_MMA_PAIR or BM_ENGINE_MMA_PAIR2, written to *engine_out.  BM_EINVAL for a NULL
  * argument or M < 1.  May query the device (cluster occupancy). */
 int bm_model_sweep_engine(bm_model m, int M, int *engine_out);
 
@@ -226,9 +226,12 @@ enum {
                                else BM_STATS_SIMT) */
     BM_STATS_SIMT = 1,      /* CUDA cores, shared-memory histograms */
     BM_STATS_MMA_BF16 = 2,  /* tensor cores, BF16 one-hot operands built in shared memory */
-    BM_STATS_MMA_FP8 = 3    /* tensor cores, FP8 E4M3 one-hot X^T written once to device memory
-                               (L*q x M rounded up to 256 bytes, owned by the chains handle) and
-                               streamed by TMA */
+    BM_STATS_MMA_FP8 = 3    /* tensor cores (CTA pairs), FP8 E4M3 one-hot X^T written once to
+                               device memory (L*q x M rounded up to 128 bytes) and streamed by
+                               TMA; on first use the chains handle also allocates a workspace for
+                               the partial counts of output tiles split along the chains
+                               (64 KB x 4 x SMs/2, ~20 MB on 152 SMs, plus its tickets); both are
+                               owned by the handle and freed with it */
 };
 
 /* Select the bm_chain_stats kernel form for these chains (all forms give
