@@ -82,6 +82,11 @@ def _load():
         "orc_pearson": (D, [P, P, P, I, I, I]),
         "orc_update": (None, [P, P, P, P, P, I, D, I, I]),
         "orc_mutant_scan": (None, [P, P, I, I, P, P]),
+        "orc_decimation_scores": (None, [P, P, P, I, I, P]),
+        "orc_activation_scores": (None, [P, P, I, I, P]),
+        "orc_graph_decimate": (ctypes.c_long, [P, P, P, I, I, ctypes.c_long]),
+        "orc_graph_activate": (ctypes.c_long, [P, P, I, I, ctypes.c_long]),
+        "orc_update_masked": (None, [P, P, P, P, P, I, D, I, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -314,3 +319,76 @@ def mutant_scan(h, J, wt) -> np.ndarray:
     dE = np.zeros((L, q), dtype=np.float64)
     _load().orc_mutant_scan(_p(h), _p(J), L, q, _p(wt), _p(dE))
     return dE
+
+
+# ---------------------------------------------------------------- sparse graphs (Sec. 2.2)
+
+def n_elements(L: int, q: int) -> int:
+    """Coupling elements (i < j, a, b), numbered pair by pair in row order."""
+    return L * (L - 1) // 2 * q * q
+
+
+def pair_freqs(counts, M: int, L: int, q: int) -> np.ndarray:
+    """Model pair frequencies p_ij(a,b) = count / M in the natural layout
+    [i][j][a][b] (both halves), from the upper block-triangle counts."""
+    C = np.asarray(counts, dtype=np.int64).reshape(-1, q, q)
+    P = np.zeros((L, L, q, q))
+    for i in range(L):
+        for j in range(i, L):
+            blk = C[i * L - i * (i - 1) // 2 + (j - i)] / M
+            P[i, j] = blk
+            P[j, i] = blk.T
+    return P
+
+
+def decimation_scores(J, pij, active) -> np.ndarray:
+    """Symmetric KL of removing each element (+inf where inactive)."""
+    J = _f64(J)
+    pij = _f64(pij)
+    active = _u8(active)
+    L, _, q, _ = J.shape
+    out = np.zeros(n_elements(L, q))
+    _load().orc_decimation_scores(_p(J), _p(pij), _p(active), L, q, _p(out))
+    return out
+
+
+def activation_scores(fij, pij) -> np.ndarray:
+    """Bernoulli KL between data and model pair frequencies of each element."""
+    fij = _f64(fij)
+    pij = _f64(pij)
+    L, _, q, _ = fij.shape
+    out = np.zeros(n_elements(L, q))
+    _load().orc_activation_scores(_p(fij), _p(pij), L, q, _p(out))
+    return out
+
+
+def graph_decimate(J, active, score, n: int):
+    """Returns copies (J', active', removed)."""
+    J = np.array(J, dtype=np.float64, copy=True, order="C")
+    active = np.array(active, dtype=np.uint8, copy=True, order="C")
+    score = _f64(score)
+    L, _, q, _ = J.shape
+    removed = _load().orc_graph_decimate(_p(J), _p(active), _p(score), L, q, int(n))
+    return J, active, int(removed)
+
+
+def graph_activate(active, score, n: int):
+    """Returns copies (active', newly_activated)."""
+    active = np.array(active, dtype=np.uint8, copy=True, order="C")
+    score = _f64(score)
+    L, _, q, _ = active.shape
+    fresh = _load().orc_graph_activate(_p(active), _p(score), L, q, int(n))
+    return active, int(fresh)
+
+
+def update_masked(h, J, fi, fij, counts, M: int, lr: float, active):
+    """Eq. 5 on a sparse graph; returns updated copies (h', J')."""
+    h = np.array(h, dtype=np.float64, copy=True, order="C")
+    J = np.array(J, dtype=np.float64, copy=True, order="C")
+    fi = _f64(fi)
+    fij = _f64(fij)
+    C = np.ascontiguousarray(counts, dtype=np.int32)
+    active = _u8(active)
+    L, q = h.shape
+    _load().orc_update_masked(_p(h), _p(J), _p(fi), _p(fij), _p(C), M, lr, L, q, _p(active))
+    return h, J

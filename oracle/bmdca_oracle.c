@@ -521,3 +521,169 @@ void orc_mutant_scan(const double *h, const double *J, int L, int q, const uint8
         }
     free(s);
 }
+
+/* ------------------------------------------------------------------------
+ * Sparse interaction graphs (Sec. 2.2, "Training sparse models").
+ *
+ * An element is one coupling entry J_ij(a,b) with i < j; its mirror
+ * J_ji(b,a) follows it.  Elements are numbered in row order: pairs (i,j),
+ * i < j, in the order (0,1), (0,2), ..., (1,2), ..., and within a pair a*q+b.
+ * `active` uses the natural layout [i][j][a][b] and is kept symmetric.
+ * ---------------------------------------------------------------------- */
+static size_t orc_n_elements(int L, int q) { return (size_t)L * (L - 1) / 2 * q * q; }
+
+/* (i, j, a, b) of element e. */
+static void orc_element(size_t e, int L, int q, int *i, int *j, int *a, int *b)
+{
+    const size_t qq = (size_t)q * q;
+    size_t p = e / qq, w = e % qq;
+    int r = 0;
+    while (p >= (size_t)(L - 1 - r)) {
+        p -= (size_t)(L - 1 - r);
+        ++r;
+    }
+    *i = r;
+    *j = r + 1 + (int)p;
+    *a = (int)(w / q);
+    *b = (int)(w % q);
+}
+
+/* Element decimation (edDCA): the score of removing an active element is
+ * the symmetric Kullback-Leibler divergence between the model P and the
+ * model P' with that element set to zero.  Removing it multiplies P(s) by
+ * e^{-J} where s_i = a and s_j = b (then renormalises), so with p = p_ij(a,b)
+ * of the model
+ *   p' = p e^{-J} / (1 - p + p e^{-J}),
+ *   KL(P||P') + KL(P'||P) = J (p - p').
+ * Reading: the paper names this criterion and leaves its evaluation to the
+ * literature; this is its exact value for one element given p.  Negative
+ * values from rounding are taken as 0.  Inactive elements score +inf.
+ * pij: model pair frequencies, natural layout [i][j][a][b]. */
+void orc_decimation_scores(const double *J, const double *pij, const uint8_t *active, int L, int q,
+                           double *score)
+{
+    const size_t n = orc_n_elements(L, q);
+    for (size_t e = 0; e < n; ++e) {
+        int i, j, a, b;
+        orc_element(e, L, q, &i, &j, &a, &b);
+        const size_t x = jidx(L, q, i, j, a, b);
+        if (!active[x]) {
+            score[e] = INFINITY;
+            continue;
+        }
+        const double Jx = J[x], p = pij[x];
+        const double w = p * exp(-Jx);
+        const double pp = w / (1.0 - p + w);
+        const double d = Jx * (p - pp);
+        score[e] = d > 0.0 ? d : 0.0;
+    }
+}
+
+/* Element activation (eaDCA): the score of an element is how far the
+ * model's pair frequency p = p_ij(a,b) is from the data's f = f_ij(a,b),
+ * measured by the Bernoulli Kullback-Leibler divergence
+ *   A = f log(f/p) + (1-f) log((1-f)/(1-p)),   0 log 0 = 0,
+ * which is also the data log-likelihood gained by fitting that single
+ * coupling with every other parameter fixed (max over d of
+ * d f - log(1 - p + p e^d)).  Reading: the paper points to the literature
+ * for "the most distant" criterion; this is the one used here.  +inf where
+ * f > 0 = p or f < 1 = p.  Every element is scored, active or not (the
+ * paper selects among all quadruplets). */
+void orc_activation_scores(const double *fij, const double *pij, int L, int q, double *score)
+{
+    const size_t n = orc_n_elements(L, q);
+    for (size_t e = 0; e < n; ++e) {
+        int i, j, a, b;
+        orc_element(e, L, q, &i, &j, &a, &b);
+        const size_t x = jidx(L, q, i, j, a, b);
+        const double f = fij[x], p = pij[x];
+        double A = 0.0;
+        if (f > 0.0) A += (p > 0.0) ? f * log(f / p) : INFINITY;
+        if (f < 1.0) A += (p < 1.0) ? (1.0 - f) * log((1.0 - f) / (1.0 - p)) : INFINITY;
+        score[e] = A > 0.0 ? A : 0.0;
+    }
+}
+
+typedef struct {
+    double s;
+    size_t e;
+} orc_scored;
+
+static int orc_cmp_asc(const void *x, const void *y)
+{
+    const orc_scored *u = (const orc_scored *)x, *v = (const orc_scored *)y;
+    if (u->s < v->s) return -1;
+    if (u->s > v->s) return 1;
+    return u->e < v->e ? -1 : (u->e > v->e ? 1 : 0);
+}
+
+static int orc_cmp_desc(const void *x, const void *y)
+{
+    const orc_scored *u = (const orc_scored *)x, *v = (const orc_scored *)y;
+    if (u->s > v->s) return -1;
+    if (u->s < v->s) return 1;
+    return u->e < v->e ? -1 : (u->e > v->e ? 1 : 0);
+}
+
+/* Remove the n active elements with the smallest decimation score (ties:
+ * lower element number first): active = 0 and J = 0 at both (i,j,a,b) and
+ * (j,i,b,a).  Returns the number removed (n, capped at the active count). */
+long orc_graph_decimate(double *J, uint8_t *active, const double *score, int L, int q, long n)
+{
+    const size_t ne = orc_n_elements(L, q);
+    orc_scored *c = (orc_scored *)malloc((ne ? ne : 1) * sizeof(orc_scored));
+    size_t m = 0;
+    for (size_t e = 0; e < ne; ++e) {
+        int i, j, a, b;
+        orc_element(e, L, q, &i, &j, &a, &b);
+        if (active[jidx(L, q, i, j, a, b)]) {
+            c[m].s = score[e];
+            c[m].e = e;
+            ++m;
+        }
+    }
+    qsort(c, m, sizeof(orc_scored), orc_cmp_asc);
+    long done = 0;
+    for (size_t k = 0; k < m && done < n; ++k, ++done) {
+        int i, j, a, b;
+        orc_element(c[k].e, L, q, &i, &j, &a, &b);
+        active[jidx(L, q, i, j, a, b)] = active[jidx(L, q, j, i, b, a)] = 0;
+        J[jidx(L, q, i, j, a, b)] = J[jidx(L, q, j, i, b, a)] = 0.0;
+    }
+    free(c);
+    return done;
+}
+
+/* Select the n elements with the largest activation score among all
+ * elements (ties: lower element number first) and make them active in both
+ * halves; elements already active stay so.  Returns how many were newly
+ * activated. */
+long orc_graph_activate(uint8_t *active, const double *score, int L, int q, long n)
+{
+    const size_t ne = orc_n_elements(L, q);
+    orc_scored *c = (orc_scored *)malloc((ne ? ne : 1) * sizeof(orc_scored));
+    for (size_t e = 0; e < ne; ++e) {
+        c[e].s = score[e];
+        c[e].e = e;
+    }
+    qsort(c, ne, sizeof(orc_scored), orc_cmp_desc);
+    long fresh = 0;
+    for (size_t k = 0; k < ne && (long)k < n; ++k) {
+        int i, j, a, b;
+        orc_element(c[k].e, L, q, &i, &j, &a, &b);
+        if (!active[jidx(L, q, i, j, a, b)]) ++fresh;
+        active[jidx(L, q, i, j, a, b)] = active[jidx(L, q, j, i, b, a)] = 1;
+    }
+    free(c);
+    return fresh;
+}
+
+/* Eq. 5 on a sparse graph: as orc_update, then every inactive coupling
+ * element is zero (inactive couplings are not parameters of the model). */
+void orc_update_masked(double *h, double *J, const double *fi, const double *fij, const int32_t *C,
+                       int M, double lr, int L, int q, const uint8_t *active)
+{
+    orc_update(h, J, fi, fij, C, M, lr, L, q);
+    for (size_t x = 0; x < (size_t)L * L * q * q; ++x)
+        if (!active[x]) J[x] = 0.0;
+}
