@@ -326,6 +326,66 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
               void *stream);
 
 /*
+ * Sparse interaction graphs (Sec. 2.2, "Training sparse models").
+ *
+ * An element is one coupling entry J_ij(a,b) with i < j; its mirror J_ji(b,a)
+ * follows it.  Elements are numbered pair by pair in row order, (0,1),
+ * (0,2), ..., (1,2), ..., and within a pair a*q + b; ties in a selection go
+ * to the lower number.  The graph is kept on the model as one activity byte
+ * per entry of J's layout [i][j][a][b] (symmetric; diagonal blocks 0).  Once
+ * a graph is enabled, bm_update writes inactive couplings as zero; the sweeps
+ * and scores read J as usual.  Memory owned by the model: L*L*q*q bytes of
+ * activity, 8 bytes per element of selection keys, a few KB more.
+ */
+
+/* Create the graph: dense != 0 makes every element active (J unchanged);
+ * dense == 0 makes none active and zeroes every coupling.  May be called
+ * again to reset.  BM_EINVAL for a NULL model; BM_ECUDA on allocation or
+ * launch failure.  Asynchronous on `stream`. */
+int bm_graph_enable(bm_model m, int dense, void *stream);
+
+/* Drop the graph (the model is fully connected again; J is not changed). */
+int bm_graph_disable(bm_model m);
+
+/* Active elements and all elements (L(L-1)/2 q^2); density = ratio.  A model
+ * without a graph counts every element as active. */
+int bm_graph_count(bm_model m, long long *n_active, long long *n_elements);
+
+/* Copy the activity bytes [L][L][q][q] to active_out (BM_HOST or BM_DEVICE;
+ * a host copy synchronises `stream`).  BM_EINVAL without a graph. */
+int bm_graph_get(bm_model m, uint8_t *active_out, int where, void *stream);
+
+/*
+ * bm_graph_decimate -- edDCA graph step: remove the n active elements (n is
+ * capped at the active count) whose removal perturbs the model least, scored
+ * by the symmetric Kullback-Leibler divergence between the model and the
+ * model without the element,
+ *     D = J (p - p'),   p' = p e^{-J} / (1 - p + p e^{-J}),
+ * p = counts / M the chains' pair frequency of the element (FP64; negative
+ * rounding taken as 0).  Removed elements become inactive and both coupling
+ * entries become 0.  counts_dev: bm_chain_stats output of the chains sampled
+ * from this model.  *removed_out = the number removed.  Synchronises
+ * `stream`.  BM_EINVAL: NULL argument, no graph, M < 1 or n < 0.
+ */
+int bm_graph_decimate(bm_model m, const int32_t *counts_dev, int M, long long n, long long *removed_out,
+                      void *stream);
+
+/*
+ * bm_graph_activate -- eaDCA graph step: among all elements select the n
+ * (capped at the element count) whose model pair frequency p = counts / M is
+ * farthest from the data's f (fij_dev from bm_data_stats), scored by the
+ * Bernoulli Kullback-Leibler divergence
+ *     A = f log(f/p) + (1-f) log((1-f)/(1-p))   (0 log 0 = 0; +inf when
+ *                                                p = 0 < f or f < 1 = p),
+ * the likelihood gain of fitting that coupling alone (FP64).  Selected
+ * elements become active (their couplings start at 0, the value they had);
+ * elements already active stay so.  *activated_out = newly activated count.
+ * Synchronises `stream`.  BM_EINVAL: NULL argument, no graph, M < 1, n < 0.
+ */
+int bm_graph_activate(bm_model m, const float *fij_dev, const int32_t *counts_dev, int M, long long n,
+                      long long *activated_out, void *stream);
+
+/*
  * bm_energy_score -- DCA energy E(s) of n sequences (Eq. 1; Sec. 4.3: low
  * energy = good sequence).  seqs_dev: device uint8[n][L]; E_dev: device
  * float[n].  FP32 accumulation (large batches, n*L >= 3.3e6, stream J

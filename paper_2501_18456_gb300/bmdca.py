@@ -70,6 +70,12 @@ SIGNATURES = {
     "bm_seq_weights_static": (_I, [_P, _I, _I, _D, _P, _P, _P]),
     "bm_data_stats": (_I, [_P, _P, _I, _I, _I, _D, _P, _P, _P]),
     "bm_update": (_I, [_P, _P, _P, _P, _I, _F, _D, _P, _P, _P]),
+    "bm_graph_enable": (_I, [_P, _I, _P]),
+    "bm_graph_disable": (_I, [_P]),
+    "bm_graph_count": (_I, [_P, _P, _P]),
+    "bm_graph_get": (_I, [_P, _P, _I, _P]),
+    "bm_graph_decimate": (_I, [_P, _P, _I, ctypes.c_longlong, _P, _P]),
+    "bm_graph_activate": (_I, [_P, _P, _P, _I, ctypes.c_longlong, _P, _P]),
     "bm_energy_score": (_I, [_P, _P, _I, _P, _P]),
     "bm_mutant_scan": (_I, [_P, _P, _I, _P, _P]),
     "bm_fields": (_I, [_P, _P, _I, _P, _I, _P]),
@@ -342,6 +348,47 @@ def bm_update(m: Model, fi: torch.Tensor, fij: torch.Tensor, counts: torch.Tenso
                            ctypes.byref(rho) if want_pearson else None, ctypes.byref(applied),
                            _stream(stream)), "bm_update")
     return (float(rho.value) if want_pearson else None), bool(applied.value)
+
+
+# ---------------------------------------------------------------- sparse graphs (Sec. 2.2)
+
+def bm_graph_enable(m: Model, dense: bool = True, stream=None):
+    """Create the model's coupling graph: all elements active (dense) or none."""
+    _check(lib().bm_graph_enable(m.handle, 1 if dense else 0, _stream(stream)), "bm_graph_enable")
+
+
+def bm_graph_disable(m: Model):
+    _check(lib().bm_graph_disable(m.handle), "bm_graph_disable")
+
+
+def bm_graph_count(m: Model) -> tuple[int, int]:
+    """(active elements, all elements i < j, a, b)."""
+    na, ne = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    _check(lib().bm_graph_count(m.handle, ctypes.byref(na), ctypes.byref(ne)), "bm_graph_count")
+    return na.value, ne.value
+
+
+def bm_graph_get(m: Model, active: torch.Tensor, stream=None):
+    """Copy the activity bytes [L][L][q][q] into a uint8 tensor."""
+    p, where = _ptr(active, torch.uint8, m.L * m.L * m.q * m.q, "active")
+    _check(lib().bm_graph_get(m.handle, p, where, _stream(stream)), "bm_graph_get")
+
+
+def bm_graph_decimate(m: Model, counts: torch.Tensor, M: int, n: int, stream=None) -> int:
+    """edDCA step: remove the n active elements of smallest symmetric KL; returns the count removed."""
+    pc = _dev(counts, torch.int32, n_blocks(m.L) * m.q * m.q, "counts")
+    out = ctypes.c_longlong(0)
+    _check(lib().bm_graph_decimate(m.handle, pc, M, int(n), ctypes.byref(out), _stream(stream)), "bm_graph_decimate")
+    return out.value
+
+
+def bm_graph_activate(m: Model, fij: torch.Tensor, counts: torch.Tensor, M: int, n: int, stream=None) -> int:
+    """eaDCA step: make the n elements of largest data/model divergence active; returns the count newly active."""
+    pf = _dev(fij, torch.float32, m.L * m.L * m.q * m.q, "fij")
+    pc = _dev(counts, torch.int32, n_blocks(m.L) * m.q * m.q, "counts")
+    out = ctypes.c_longlong(0)
+    _check(lib().bm_graph_activate(m.handle, pf, pc, M, int(n), ctypes.byref(out), _stream(stream)), "bm_graph_activate")
+    return out.value
 
 
 def bm_energy_score(m: Model, seqs: torch.Tensor, E: torch.Tensor, stream=None):

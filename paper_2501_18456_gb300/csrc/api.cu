@@ -35,6 +35,10 @@ void free_model(bm_model_s *m)
     cudaFree(m->Jc);
     cudaFree(m->dflags);
     cudaFree(m->dred);
+    cudaFree(m->active);
+    cudaFree(m->gkeys);
+    cudaFree(m->gtile);
+    cudaFree(m->ghist);
     delete m;
 }
 }  // namespace

@@ -58,6 +58,16 @@ struct bm_model_s {
     double *dred = nullptr;      // reduction partials, capacity red_cap doubles
     size_t red_cap = 0;
     int num_sms = 0;
+    // Sparse interaction graph (bm_graph_enable; null: fully connected): the
+    // activity of every entry of J's layout [i][j][a][b] (symmetric), the
+    // number of active elements i < j, and the selection's scratch (one
+    // 64-bit key per element, per-tile tie counts, a 256-bin histogram
+    // followed by one 64-bit counter).
+    uint8_t *active = nullptr;
+    long long n_active = 0;
+    unsigned long long *gkeys = nullptr;
+    long long *gtile = nullptr;
+    unsigned int *ghist = nullptr;
 };
 
 struct bm_chains_s {

@@ -12,7 +12,8 @@
 // elements), each thread loading up to 16 elements of each array with
 // independent coalesced loads.  The new blocks are staged in shared memory
 // and their transposed (j,i) copies are written in destination order, so
-// both writes are coalesced.  Each thread adds its x, y terms with
+// both writes are coalesced.  On a sparse graph (Sec. 2.2) inactive
+// couplings are written as zero.  Each thread adds its x, y terms with
 // Kahan-compensated FP32 sums (x and y themselves are FP32, the precision
 // of their inputs), the threads are reduced in FP64, and the per-CTA partial
 // moments go to a scratch array that a single-CTA kernel sums in a fixed
@@ -51,8 +52,8 @@ struct Kahan {
 
 __global__ void __launch_bounds__(kUpdThreads) k_update_rows(
     const float *__restrict__ J, float *__restrict__ Jn, const float *__restrict__ fi,
-    const float *__restrict__ fij, const int32_t *__restrict__ C, int L, int q, float invM,
-    float lr, int want_pearson, long long ntiles, double *__restrict__ partials)
+    const float *__restrict__ fij, const int32_t *__restrict__ C, const uint8_t *__restrict__ active, int L, int q,
+    float invM, float lr, int want_pearson, long long ntiles, double *__restrict__ partials)
 {
     __shared__ float tile[kUpdElems];           // new J of the tile's blocks, (jj, a, b) order
     __shared__ float fj[kUpdElems / 2], pj[kUpdElems / 2];  // f_j(b), p_j(b) of the tile's blocks
@@ -87,7 +88,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_update_rows(
         for (int e = tid; e < nel; e += kUpdThreads) {
             const float f = fij[baseJ + e];
             const float pij = (float)C[baseC + e] * invM;
-            const float v = fmaf(lr, f - pij, J[baseJ + e]);
+            // Eq. 5; on a sparse graph an inactive coupling stays zero
+            const float v = (active && !active[baseJ + e]) ? 0.0f : fmaf(lr, f - pij, J[baseJ + e]);
             Jn[baseJ + e] = v;
             tile[e] = v;
             if (want_pearson) {
@@ -191,7 +193,7 @@ int bm_launch_update(bm_model_s *m, const float *fi, const float *fij, const int
     const int L = m->L, q = m->q;
     const float invM = 1.0f / (float)M;
     if (L >= 2) {
-        k_update_rows<<<nparts, kUpdThreads, 0, st>>>(m->J, m->J_back, fi, fij, counts, L, q, invM, lr,
+        k_update_rows<<<nparts, kUpdThreads, 0, st>>>(m->J, m->J_back, fi, fij, counts, m->active, L, q, invM, lr,
                                                       want_pearson, bm_update_num_tiles(L, q), partials);
         BM_CK_LAUNCH("k_update_rows");
     }
