@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-models leg")
     ap.add_argument("--no-split", action="store_true", help="skip the split-precision leg")
     ap.add_argument("--no-train", action="store_true", help="skip the training-to-target run")
+    ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-graph (edDCA / eaDCA) leg")
     ap.add_argument("--serve-requests", type=int, default=1000,
                     help="requests per engine in the serving stream (Poisson, --serve-rate per s)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
@@ -245,6 +246,67 @@ def run_reference(args, rank):
 
 
 # ----------------------------------------------------------------- GPU arm
+
+def sparse_leg(bmdca, model, fi, fij, L, q, M, seed):
+    """Sparse-graph steps (Sec. 2.2) at the bench shape, on a copy of the
+    trained model: one edDCA decimation step at the paper's default rate
+    (1 % of the active elements), a short edDCA run (10 graph steps, each
+    followed by gsteps = 10 parameter updates with 10 sweeps before each),
+    and one eaDCA activation step on an empty graph (0.1 % of the elements).
+    The graph calls synchronise their stream (the selection is host-driven),
+    so their times are CUDA-event times that include those round trips."""
+    import torch
+
+    dev = "cuda"
+    h = torch.empty((L, q), dtype=torch.float32, device=dev)
+    J = torch.empty((L, L, q, q), dtype=torch.float32, device=dev)
+    bmdca.bm_potts_get(model, h, J)
+    m = bmdca.bm_potts_load(h, J)
+    del h, J
+    c = bmdca.bm_chains_init(m, M, seed + 7)
+    bmdca.bm_gibbs_sweep(m, c, 10, 1.0)
+    counts = torch.empty((bmdca.n_blocks(L), q, q), dtype=torch.int32, device=dev)
+    bmdca.bm_chain_stats(c, counts)
+    st = torch.cuda.current_stream()
+
+    def timed_call(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        r = fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    bmdca.bm_graph_enable(m, True)
+    na, ne = bmdca.bm_graph_count(m)
+    removed, dec_ms = timed_call(lambda: bmdca.bm_graph_decimate(m, counts, M, int(0.01 * na)))
+    gsteps, nsw, nsteps = 10, 10, 10
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(nsteps):
+        bmdca.bm_graph_decimate(m, counts, M, int(0.01 * bmdca.bm_graph_count(m)[0]))
+        for _ in range(gsteps):
+            bmdca.bm_gibbs_sweep(m, c, nsw, 1.0)
+            bmdca.bm_chain_stats(c, counts)
+            bmdca.bm_update(m, fi, fij, counts, M, LR, 2.0, False)
+    b.record(st)
+    torch.cuda.synchronize()
+    run_ms = a.elapsed_time(b)
+    density = bmdca.bm_graph_count(m)[0] / ne
+    bmdca.bm_graph_enable(m, False)
+    bmdca.bm_chain_stats(c, counts)
+    activated, act_ms = timed_call(lambda: bmdca.bm_graph_activate(m, fij, counts, M, int(0.001 * ne)))
+    bmdca.bm_device_status(m)
+    del m, c, counts
+    return {"elements": ne, "decimate_ms": dec_ms, "decimate_removed": removed,
+            "activate_ms": act_ms, "activated": activated,
+            "eddca_graph_steps": nsteps, "gsteps": gsteps, "nsweeps": nsw,
+            "eddca_ms_per_graph_step": run_ms / nsteps, "eddca_density_after": density,
+            "note": "graph steps select exactly n elements by FP64 score (symmetric KL for "
+                    "decimation, Bernoulli KL for activation), ties by element number"}
+
 
 def split_precision_leg(bmdca, synth, timed):
     """Split-precision RNA-like shape (L=120, q=5, M=20,000): the sweep with
@@ -555,6 +617,12 @@ def run_ours(args, rank, world, local):
         del m2, c2, JT, Jp, a_, b_
         torch.cuda.empty_cache()
 
+    # ---- sparse graphs (edDCA / eaDCA steps) on a copy of the model (rank 0)
+    sparse = None
+    if rank == 0 and not args.no_sparse:
+        sparse = sparse_leg(bmdca, model, fi, fij, L_SITES, Q, M_CHAINS, seed)
+        torch.cuda.empty_cache()
+
     # ---- serving: Poisson streams of sample / score / mutant-scan requests over
     # 32 resident models through the continuous-batching server (rank 0), with
     # the default engines and with plain FP32 sampling; then the same mix
@@ -621,7 +689,8 @@ def run_ours(args, rank, world, local):
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps,
                 "clocks": clk, "rows_ms": rows, "train_to_target": train_run,
-                "split_precision": split, "serve": serve, "batched": batched, "wall_s_timed": t_wall}
+                "split_precision": split, "sparse": sparse, "serve": serve, "batched": batched,
+                "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
