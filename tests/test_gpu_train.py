@@ -106,3 +106,61 @@ def test_training_reaches_target_and_learns_planted_couplings(bm, planted, data,
     r = np.corrcoef(Jp[iu].ravel(), Jl[iu].ravel())[0, 1]
     assert r > 0.75, r
     assert np.array_equal(J_learned.cpu().numpy(), J_learned.cpu().numpy().transpose(1, 0, 3, 2))
+
+
+def _near_far_fraction(act):
+    """Active fraction of the elements of planted pairs (|i-j| <= 3) and of the others."""
+    I, Jj = np.triu_indices(L, 1)
+    near = (Jj - I) <= 3
+    per_pair = act[I, Jj].reshape(len(I), -1).mean(axis=1)
+    return per_pair[near].mean(), per_pair[~near].mean()
+
+
+def test_eddca_prunes_to_the_density_keeping_the_planted_couplings(bm, data):
+    """Sec. 2.2, edDCA: from a model trained to the target, decimate until
+    the density is reached, converging on every graph before pruning it."""
+    cfg = train.TrainConfig(M=16384, nsweeps=10, lr=LR, max_iters=150, target=0.95, reweight=False,
+                            pseudocount=1.0 / N)
+    msa = torch.from_numpy(np.ascontiguousarray(data)).to(DEV)
+    stats = train.data_statistics(msa, Q, cfg)
+    h0, J0 = train.profile_init(stats)
+    m = bm.bm_potts_load(h0, J0)
+    c = bm.bm_chains_init(m, cfg.M, 3)
+    hist = train.train(m, c, stats, cfg)
+    assert hist[-1]["pearson"] >= 0.95
+    recs = train.eddca(m, c, stats, cfg, density=0.3, drate=0.1, gsteps=10, max_rounds=300)
+    bm.bm_device_status(m)
+    na, ne = bm.bm_graph_count(m)
+    assert na <= 0.3 * ne
+    assert recs and all(r["pearson_before"] >= 0.95 for r in recs), [r["pearson_before"] for r in recs]
+    act = torch.empty((L, L, Q, Q), dtype=torch.uint8)
+    bm.bm_graph_get(m, act)
+    act = act.numpy()
+    Jm = torch.empty((L, L, Q, Q), dtype=torch.float32)
+    bm.bm_potts_get(m, None, Jm)
+    torch.cuda.synchronize()
+    assert np.all(Jm.numpy()[act == 0] == 0.0)
+    near, far = _near_far_fraction(act)
+    assert near > 2 * far, (near, far)
+
+
+def test_eadca_grows_the_graph_on_the_planted_couplings(bm, data):
+    """Sec. 2.2, eaDCA: from the profile model and an empty graph, activate
+    elements step by step; the fit improves and the activated elements are
+    mostly those of the planted pairs."""
+    cfg = train.TrainConfig(M=16384, nsweeps=10, lr=LR, max_iters=0, target=0.95, reweight=False,
+                            pseudocount=1.0 / N)
+    msa = torch.from_numpy(np.ascontiguousarray(data)).to(DEV)
+    stats = train.data_statistics(msa, Q, cfg)
+    h0, J0 = train.profile_init(stats)
+    m = bm.bm_potts_load(h0, J0)
+    c = bm.bm_chains_init(m, cfg.M, 4)
+    recs = train.eadca(m, c, stats, cfg, factivate=0.02, gsteps=10, max_graph_steps=40)
+    bm.bm_device_status(m)
+    rho = [r["pearson"] for r in recs]
+    assert rho[-1] > 0.8 and rho[-1] > rho[0] + 0.3, rho
+    act = torch.empty((L, L, Q, Q), dtype=torch.uint8)
+    bm.bm_graph_get(m, act)
+    near, far = _near_far_fraction(act.numpy())
+    assert near > 2 * far, (near, far)
+    assert all(r["density"] <= 1.0 for r in recs)
