@@ -50,6 +50,7 @@ struct Kahan {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+template <bool MASKED>  // MASKED: a sparse graph is enabled (inactive couplings written as zero)
 __global__ void __launch_bounds__(kUpdThreads) k_update_rows(
     const float *__restrict__ J, float *__restrict__ Jn, const float *__restrict__ fi,
     const float *__restrict__ fij, const int32_t *__restrict__ C, const uint8_t *__restrict__ active, int L, int q,
@@ -89,7 +90,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_update_rows(
             const float f = fij[baseJ + e];
             const float pij = (float)C[baseC + e] * invM;
             // Eq. 5; on a sparse graph an inactive coupling stays zero
-            const float v = (active && !active[baseJ + e]) ? 0.0f : fmaf(lr, f - pij, J[baseJ + e]);
+            float v = fmaf(lr, f - pij, J[baseJ + e]);
+            if (MASKED && !active[baseJ + e]) v = 0.0f;
             Jn[baseJ + e] = v;
             tile[e] = v;
             if (want_pearson) {
@@ -193,8 +195,9 @@ int bm_launch_update(bm_model_s *m, const float *fi, const float *fij, const int
     const int L = m->L, q = m->q;
     const float invM = 1.0f / (float)M;
     if (L >= 2) {
-        k_update_rows<<<nparts, kUpdThreads, 0, st>>>(m->J, m->J_back, fi, fij, counts, m->active, L, q, invM, lr,
-                                                      want_pearson, bm_update_num_tiles(L, q), partials);
+        auto *kern = m->active ? k_update_rows<true> : k_update_rows<false>;
+        kern<<<nparts, kUpdThreads, 0, st>>>(m->J, m->J_back, fi, fij, counts, m->active, L, q, invM, lr, want_pearson,
+                                             bm_update_num_tiles(L, q), partials);
         BM_CK_LAUNCH("k_update_rows");
     }
     k_update_fields<<<(L * q + 255) / 256, 256, 0, st>>>(m->h, m->h_back, fi, counts, L, q, invM,
