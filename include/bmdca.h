@@ -32,6 +32,11 @@
  *     last failure.  Invalid arguments are rejected before any GPU work.
  *   - Limits: 1 <= q <= 32, 1 <= L <= 4096, M >= 1.
  *   - Handles are not thread-safe: one host thread at a time per handle.
+ *     Work on one handle must also not overlap across streams: a handle's
+ *     scratch (derived coupling layouts, the chain counts' one-hot operand,
+ *     split-tile partials and tickets, the graph selection keys) is reused
+ *     by every call, so calls on different streams need the caller's
+ *     ordering (an event) between them.
  *
  * Random numbers: every draw uses Philox4x64-10 (Salmon et al., SC'11) with
  * key (seed, 0) and counter (chain, sweep, site, tag), tag 0 for Gibbs
