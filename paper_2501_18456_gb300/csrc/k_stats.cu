@@ -342,88 +342,163 @@ __device__ __forceinline__ void pair_words(const uint4 (&a)[4][2], const uint4 (
         }
 }
 
-__global__ void __launch_bounds__(256) k_identity_bs(const uint32_t *__restrict__ planes,
-                                                     const unsigned *__restrict__ used, int N, int L, int Lw,
-                                                     int thr, int ntile, int *__restrict__ cnt)
+// Position in the row-major enumeration of the upper triangle of tile pairs,
+// advanced by a fixed stride without re-walking the rows.
+struct TriCursor {
+    int r, rem;  // tile pair (r, r + rem)
+    __device__ __forceinline__ void init(long long t, int nt)
+    {
+        r = 0;
+        long long x = t;
+        while (r < nt && x >= nt - r) {
+            x -= nt - r;
+            ++r;
+        }
+        rem = (int)x;
+    }
+    __device__ __forceinline__ void advance(int by, int nt)
+    {
+        long long x = (long long)rem + by;
+        while (r < nt && x >= nt - r) {
+            x -= nt - r;
+            ++r;
+        }
+        rem = (int)x;
+    }
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid)
 {
-    constexpr int kRow4 = 2 * kBWChunk + 1;  // uint4 per staged sequence (odd: conflict-free 128-bit reads)
-    __shared__ uint4 A[kWT][kRow4];
-    __shared__ uint4 B[kWT][kRow4];
-    __shared__ int cntA[kWT], cntB[kWT];
-    int tm, tn;
-    tile_pair_from_index(blockIdx.x, ntile, tm, tn);
-    const int m0 = tm * kWT, n0 = tn * kWT;
+    // src-size 0 fills the 16 bytes with zeros (rows past N, words past Lw)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+constexpr int kIdRow4 = 2 * kBWChunk + 1;  // uint4 per staged sequence (odd: conflict-free 128-bit reads)
+constexpr int kIdBlocksPerSM = 2;          // latency is hidden by the double buffer, not by occupancy
+constexpr size_t kIdSmem = (size_t)2 * 2 * kWT * kIdRow4 * sizeof(uint4) + 2 * kWT * sizeof(int);
+
+// Persistent over tile pairs (64 x 64 sequences) and their 256-position
+// chunks: the next step's planes are copied into the other half of a
+// double buffer (cp.async) while this step's pairs are compared, so the
+// loads of a tile pair overlap the comparisons of the previous one.
+__global__ void __launch_bounds__(256, kIdBlocksPerSM) k_identity_bs(const uint32_t *__restrict__ planes,
+                                                                     const unsigned *__restrict__ used, int N, int L,
+                                                                     int Lw, int thr, int ntile, long long npairs,
+                                                                     int *__restrict__ cnt)
+{
+    extern __shared__ __align__(16) unsigned char id_smem[];
+    uint4 *buf = reinterpret_cast<uint4 *>(id_smem);  // [2 halves][A, B][kWT][kIdRow4]
+    int *cntA = reinterpret_cast<int *>(buf + 2 * 2 * kWT * kIdRow4);
+    int *cntB = cntA + kWT;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 4 x 4 pairs each
     const bool five = (*used >> 5) == 0u;                    // every symbol < 32
-    int mism[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) mism[u][v] = 0;
+    const uint4 *P4 = reinterpret_cast<const uint4 *>(planes);
+    const int nch = (Lw + kBWChunk - 1) / kBWChunk;
+    const long long mine = blockIdx.x < npairs ? (npairs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long steps = mine * nch;
     if (threadIdx.x < kWT) {
         cntA[threadIdx.x] = 0;
         cntB[threadIdx.x] = 0;
     }
-    const uint4 *P4 = reinterpret_cast<const uint4 *>(planes);
-    const uint4 zero = make_uint4(0, 0, 0, 0);
-    for (int w0 = 0; w0 < Lw; w0 += kBWChunk) {
+    TriCursor cc, pc;  // tile pair being compared / being fetched
+    cc.init(blockIdx.x, ntile);
+    pc = cc;
+    int cch = 0, pch = 0;  // their chunks
+    auto fetch = [&](int half) {
+        const int m0 = pc.r * kWT, n0 = (pc.r + pc.rem) * kWT, w0 = pch * kBWChunk;
         const int nw = min(kBWChunk, Lw - w0);
-        __syncthreads();
+        uint4 *A = buf + (size_t)half * 2 * kWT * kIdRow4, *B = A + kWT * kIdRow4;
         for (int k = threadIdx.x; k < kWT * 2 * kBWChunk; k += blockDim.x) {
             const int r = k / (2 * kBWChunk), c2 = k % (2 * kBWChunk);
             const int ma = m0 + r, nb = n0 + r;
             const bool in = (c2 >> 1) < nw;
-            A[r][c2] = (in && ma < N) ? P4[((size_t)ma * Lw + w0) * 2 + c2] : zero;
-            B[r][c2] = (in && nb < N) ? P4[((size_t)nb * Lw + w0) * 2 + c2] : zero;
+            const bool va = in && ma < N, vb = in && nb < N;
+            cp_async16((uint32_t)__cvta_generic_to_shared(A + r * kIdRow4 + c2),
+                       va ? P4 + ((size_t)ma * Lw + w0) * 2 + c2 : P4, va);
+            cp_async16((uint32_t)__cvta_generic_to_shared(B + r * kIdRow4 + c2),
+                       vb ? P4 + ((size_t)nb * Lw + w0) * 2 + c2 : P4, vb);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (++pch == nch) {
+            pch = 0;
+            pc.advance(gridDim.x, ntile);
+        }
+    };
+    int mism[4][4];
+    if (steps > 0) fetch(0);
+    for (long long s = 0; s < steps; ++s) {
+        if (s + 1 < steps) {
+            fetch((int)((s + 1) & 1));
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
+        if (cch == 0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) mism[u][v] = 0;
+        }
+        const uint4 *A = buf + (size_t)(s & 1) * 2 * kWT * kIdRow4, *B = A + kWT * kIdRow4;
+        const int nw = min(kBWChunk, Lw - cch * kBWChunk);
         for (int c = 0; c < nw; ++c) {
             uint4 ra[4][2], rb[4][2];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                ra[u][0] = A[ty + 16 * u][2 * c];
-                ra[u][1] = A[ty + 16 * u][2 * c + 1];
+                ra[u][0] = A[(ty + 16 * u) * kIdRow4 + 2 * c];
+                ra[u][1] = A[(ty + 16 * u) * kIdRow4 + 2 * c + 1];
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                rb[v][0] = B[tx + 16 * v][2 * c];
-                rb[v][1] = B[tx + 16 * v][2 * c + 1];
+                rb[v][0] = B[(tx + 16 * v) * kIdRow4 + 2 * c];
+                rb[v][1] = B[(tx + 16 * v) * kIdRow4 + 2 * c + 1];
             }
             if (five)
                 pair_words<5>(ra, rb, mism);
             else
                 pair_words<8>(ra, rb, mism);
         }
-    }
-    // Credit qualifying pairs (identity = L - mismatches >= thr).
+        if (cch == nch - 1) {
+            // Credit qualifying pairs (identity = L - mismatches >= thr).
+            const int tm = cc.r, tn = cc.r + cc.rem, m0 = tm * kWT, n0 = tn * kWT;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int rm = ty + 16 * u, rn = tx + 16 * v;
-            const int m = m0 + rm, n = n0 + rn;
-            if (m >= N || n >= N || L - mism[u][v] < thr) continue;
-            if (tm == tn) {
-                if (rm < rn) {
-                    atomicAdd(&cntA[rm], 1);
-                    atomicAdd(&cntB[rn], 1);
-                } else if (rm == rn) {
-                    atomicAdd(&cntA[rm], 1);  // self-identity, counted once
+                for (int v = 0; v < 4; ++v) {
+                    const int rm = ty + 16 * u, rn = tx + 16 * v;
+                    const int m = m0 + rm, n = n0 + rn;
+                    if (m >= N || n >= N || L - mism[u][v] < thr) continue;
+                    if (tm == tn) {
+                        if (rm < rn) {
+                            atomicAdd(&cntA[rm], 1);
+                            atomicAdd(&cntB[rn], 1);
+                        } else if (rm == rn) {
+                            atomicAdd(&cntA[rm], 1);  // self-identity, counted once
+                        }
+                    } else {
+                        atomicAdd(&cntA[rm], 1);
+                        atomicAdd(&cntB[rn], 1);
+                    }
                 }
-            } else {
-                atomicAdd(&cntA[rm], 1);
-                atomicAdd(&cntB[rn], 1);
+            __syncthreads();
+            if (threadIdx.x < kWT) {
+                const int m = m0 + threadIdx.x, n = n0 + threadIdx.x;
+                if (m < N && cntA[threadIdx.x]) atomicAdd(&cnt[m], cntA[threadIdx.x]);
+                if (n < N && cntB[threadIdx.x]) atomicAdd(&cnt[n], cntB[threadIdx.x]);
+                cntA[threadIdx.x] = 0;
+                cntB[threadIdx.x] = 0;
             }
         }
-    __syncthreads();
-    if (threadIdx.x < kWT) {
-        const int m = m0 + threadIdx.x, n = n0 + threadIdx.x;
-        if (m < N && cntA[threadIdx.x]) atomicAdd(&cnt[m], cntA[threadIdx.x]);
-        if (n < N && cntB[threadIdx.x]) atomicAdd(&cnt[n], cntB[threadIdx.x]);
+        __syncthreads();  // this half is refilled by the fetch two steps on
+        if (++cch == nch) {
+            cch = 0;
+            cc.advance(gridDim.x, ntile);
+        }
     }
 }
 
-// w = 1 / N_m; M_eff = sum w in FP64 (one CTA, fixed order => deterministic).
 __global__ void k_weights_finalize(const int *__restrict__ cnt, int N, float *__restrict__ w,
                                    double *meff)
 {
@@ -537,8 +612,12 @@ int bm_launch_seq_weights_bs(const uint8_t *msa, int N, int L, int thr, float *w
     BM_CK_LAUNCH("k_bitslice");
     const int ntile = (N + kWT - 1) / kWT;
     const long long npairs = (long long)ntile * (ntile + 1) / 2;
-    if (npairs > 0x7fffffffLL) return bm_fail(BM_EINVAL, "bm_seq_weights: N too large");
-    k_identity_bs<<<(unsigned)npairs, 256, 0, st>>>(planes, used, N, L, Lw, thr, ntile, cnt);
+    int dev = 0, nsm = 0;
+    BM_CK(cudaGetDevice(&dev));
+    BM_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    BM_CK(cudaFuncSetAttribute(k_identity_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdSmem));
+    const int grid = (int)std::max<long long>(1, std::min<long long>(npairs, (long long)nsm * kIdBlocksPerSM));
+    k_identity_bs<<<grid, 256, kIdSmem, st>>>(planes, used, N, L, Lw, thr, ntile, npairs, cnt);
     BM_CK_LAUNCH("k_identity_bs");
     k_weights_finalize<<<1, 1024, 0, st>>>(cnt, N, w, meff_dev);
     BM_CK_LAUNCH("k_weights_finalize");
