@@ -378,6 +378,37 @@ constexpr int kIdRow4 = 2 * kBWChunk + 1;  // uint4 per staged sequence (odd: co
 constexpr int kIdBlocksPerSM = 2;          // latency is hidden by the double buffer, not by occupancy
 constexpr size_t kIdSmem = (size_t)2 * 2 * kWT * kIdRow4 * sizeof(uint4) + 2 * kWT * sizeof(int);
 
+// The 4 x 4 pairs of one thread over nw staged words; only the planes in
+// use are loaded (five: planes 0-3 as one 16-byte word and plane 4 as 4
+// bytes, which cuts the shared-memory wavefronts of the loads).
+template <int NP>
+__device__ __forceinline__ void compare_chunk(const uint4 *__restrict__ A, const uint4 *__restrict__ B, int nw,
+                                              int ty, int tx, int (&mism)[4][4])
+{
+    for (int c = 0; c < nw; ++c) {
+        uint4 ra[4][2], rb[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint4 *pa = A + (ty + 16 * u) * kIdRow4 + 2 * c;
+            ra[u][0] = pa[0];
+            if (NP > 4) {
+                if (NP > 5) ra[u][1] = pa[1];
+                else ra[u][1].x = reinterpret_cast<const uint32_t *>(pa + 1)[0];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const uint4 *pb = B + (tx + 16 * v) * kIdRow4 + 2 * c;
+            rb[v][0] = pb[0];
+            if (NP > 4) {
+                if (NP > 5) rb[v][1] = pb[1];
+                else rb[v][1].x = reinterpret_cast<const uint32_t *>(pb + 1)[0];
+            }
+        }
+        pair_words<NP>(ra, rb, mism);
+    }
+}
+
 // Persistent over tile pairs (64 x 64 sequences) and their 256-position
 // chunks: the next step's planes are copied into the other half of a
 // double buffer (cp.async) while this step's pairs are compared, so the
@@ -443,23 +474,10 @@ __global__ void __launch_bounds__(256, kIdBlocksPerSM) k_identity_bs(const uint3
         }
         const uint4 *A = buf + (size_t)(s & 1) * 2 * kWT * kIdRow4, *B = A + kWT * kIdRow4;
         const int nw = min(kBWChunk, Lw - cch * kBWChunk);
-        for (int c = 0; c < nw; ++c) {
-            uint4 ra[4][2], rb[4][2];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                ra[u][0] = A[(ty + 16 * u) * kIdRow4 + 2 * c];
-                ra[u][1] = A[(ty + 16 * u) * kIdRow4 + 2 * c + 1];
-            }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                rb[v][0] = B[(tx + 16 * v) * kIdRow4 + 2 * c];
-                rb[v][1] = B[(tx + 16 * v) * kIdRow4 + 2 * c + 1];
-            }
-            if (five)
-                pair_words<5>(ra, rb, mism);
-            else
-                pair_words<8>(ra, rb, mism);
-        }
+        if (five)
+            compare_chunk<5>(A, B, nw, ty, tx, mism);
+        else
+            compare_chunk<8>(A, B, nw, ty, tx, mism);
         if (cch == nch - 1) {
             // Credit qualifying pairs (identity = L - mismatches >= thr).
             const int tm = cc.r, tn = cc.r + cc.rem, m0 = tm * kWT, n0 = tn * kWT;
