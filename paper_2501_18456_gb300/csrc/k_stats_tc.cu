@@ -32,14 +32,14 @@
 //                  tiles; the R = ntiles mod npairs remaining tiles are split
 //                  into s parts along the chains, one part per pair, taken
 //                  first, so every pair ends after about ntiles / npairs
-//                  tiles.  A part's
-//                  epilogue writes its int32 partial counts to a workspace
-//                  and takes a ticket (device-scope atomic after a fence; the
-//                  ticket word carries the launch's epoch, so a ticket left by
-//                  an earlier launch counts as none); the part that draws the
-//                  last ticket adds the other partials to its own accumulator
-//                  and stores the sums.  No part waits on another, and the
-//                  sums are exact in any order.
+//                  tiles.  A part's epilogue writes its int32 partial counts
+//                  to a workspace, releases its accumulator and takes a
+//                  ticket (device-scope CAS after a fence; the ticket word
+//                  carries the launch's epoch, so a ticket left by an earlier
+//                  launch counts as none); the part that draws the last
+//                  ticket sums all the partials from the workspace and stores
+//                  them while its pair's next tile accumulates.  No part waits
+//                  on another, and the sums are exact in any order.
 // Every mbarrier wait is bounded by %globaltimer (2 s); a timeout sets the
 // chains' device error word (bit 2), every role leaves its loop and TMEM is
 // released.
