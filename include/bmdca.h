@@ -339,7 +339,9 @@ int bm_update(bm_model m, const float *fi_data, const float *fij_data, const int
  * to the lower number.  The graph is kept on the model as one activity byte
  * per entry of J's layout [i][j][a][b] (symmetric; diagonal blocks 0).  Once
  * a graph is enabled, bm_update writes inactive couplings as zero; the sweeps
- * and scores read J as usual.  Memory owned by the model: L*L*q*q bytes of
+ * and scores read J as usual.  bm_potts_set stores J as given, inactive
+ * entries included, and does not change the graph; the next bm_update zeroes
+ * the inactive couplings again.  Memory owned by the model: L*L*q*q bytes of
  * activity, 8 bytes per element of selection keys, a few KB more.
  */
 
