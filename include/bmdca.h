@@ -40,7 +40,8 @@
  *
  * Random numbers: every draw uses Philox4x64-10 (Salmon et al., SC'11) with
  * key (seed, 0) and counter (chain, sweep, site, tag), tag 0 for Gibbs
- * draws and tag 1 for chain initialisation; the uniform is the top 24 bits
+ * draws, tag 1 for chain initialisation, tags 2 and 3 for the Metropolis
+ * proposal and acceptance (bm_model_set_sampler); the uniform is the top 24 bits
  * of output word 0 scaled by 2^-24.  Results therefore depend only on the
  * seed and the global chain / sweep / site indices, not on launch shapes.
  */
