@@ -386,7 +386,8 @@ def test_chain_stats_bit_exact(bm, orc, M, L, q, engine):
     assert np.array_equal(counts.cpu().numpy(), orc.chain_stats(S, q))
 
 
-@pytest.mark.parametrize("M,L,q", [(1024, 16, 21), (333, 37, 5), (129, 300, 21)])
+@pytest.mark.parametrize("M,L,q", [(1024, 16, 21), (333, 37, 5), (129, 300, 21), (3000, 200, 21),
+                                   (257, 1000, 4)])
 def test_chain_stats_repeated_calls_on_one_handle(bm, orc, M, L, q):
     """Calls of the FP8 form on one chains handle, with sweeps between them:
     at these shapes some output tiles are split along the chains and summed
@@ -521,7 +522,7 @@ def test_data_stats_rejects_bad_symbols(bm):
 # ---------------------------------------------------------------- update + pearson
 
 @pytest.mark.parametrize("L,q,M", [(16, 21, 1024), (37, 5, 333), (2, 3, 10), (100, 21, 400), (9, 1, 20),
-                                   (130, 2, 64)])
+                                   (130, 2, 64), (600, 5, 300), (257, 21, 100)])
 def test_update_and_pearson_parity(bm, orc, L, q, M):
     h, J = synth.planted_local_model(L, q, 8)
     m = load(bm, h, J)
