@@ -582,6 +582,16 @@ def run_ours(args, rank, world, local):
                        "frac": cs_ach / (2 * peak_tf), "kernel": "k_onehot_t + k_counts_pair",
                        "note": "achieved = 2*M*(L(L+1)/2)*q^2 flops / CUDA-event time of bm_chain_stats "
                                "(one-hot build included); peak: fp8 = 2 x " + peak_src + " bf16_tflops (burst)"}
+    # update + Pearson: 16 B per coupling parameter (read J and f_ij, the
+    # counts, write the new J) over the L^2 q^2 parameters; the time is the
+    # whole call, including the read-back of the Pearson moments
+    upd_bytes = 16.0 * (L_SITES * Q) ** 2
+    peak_hbm = float(peaks.get("hbm_gbs", 6800.0))
+    upd_ach = upd_bytes / (rows["update_pearson_ms"] * 1e-3) / 1e9
+    roofline_update = {"bound": "hbm", "achieved": upd_ach, "peak": peak_hbm, "unit": "GB/s",
+                       "frac": upd_ach / peak_hbm, "kernel": "k_update_rows + k_update_fields + k_sum_partials",
+                       "note": "achieved = 16 B x (L q)^2 parameters / CUDA-event time of bm_update with the Pearson "
+                               "check (moments read back to the host); peak: " + peak_src + " hbm_gbs"}
 
     # ---- split precision (RNA-like shape), rank 0
     split = None
@@ -691,7 +701,7 @@ def run_ours(args, rank, world, local):
                                "ms_per_step": ms_plain, "gibbs_ms_per_sweep": ms_plain_gibbs / NSWEEPS,
                                "engine": "CUDA-core FP32 gather (k_gibbs_staged)",
                                "speedup_of_value": ms_plain / ms_step},
-                "roofline": roofline, "roofline_chain_stats": roofline_counts, "cpu_baseline": cpu,
+                "roofline": roofline, "roofline_chain_stats": roofline_counts, "roofline_update": roofline_update, "cpu_baseline": cpu,
                 "e2e": {"value": world * site_updates_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps,
